@@ -1,0 +1,321 @@
+"""Benchmark: Richardson-Lucy deconvolution throughput on one GB300.
+
+Workload (one "step"): the 2048 x 2048 FP32 synthetic image deconvolved with
+each of the three PSFs of the plain-RL workload -- horizontal motion length
+31, vertical motion length 31, and a disc of radius 8 -- for 200 iterations
+each (Poisson noise at peak 1000, mirror boundaries, u0 = f, no thinning),
+every solve on its production path (running sum, running sum, span).
+Metric: Mpixel-iterations per second (3 x 2048^2 x 200 pixel-iterations per
+step).
+
+``value`` times the device path with inputs already resident in HBM; ``e2e``
+times the same call through the C ABI with pinned HOST buffers, so the library
+stages f and u in and out inside the timed region.  Under torchrun every rank
+runs its own replica (the solves are independent; no collective on the data
+path) and ``value`` sums all ranks' work over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel-iter/s per GB300 vs plain path at <=1e-4 rel err; serve p50/p99 ms"
+UNIT = "Mpixel-iter/s"
+SIZE = 2048
+ITERS = 200
+WORKLOAD = "plain RL 2048x2048 fp32, PSFs motion-x 31 / motion-y 31 / disc r8, 200 it each"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    import numpy as np
+    from paper_1304_7211_gb300 import synth
+    out = []
+    for spec in synth.CONFIG2_PSFS:
+        c = synth.config2(spec, SIZE)
+        out.append((spec, c.f.astype(np.float32)))
+    return out
+
+
+def cpu_baseline_run(inputs, budget_s: float = 20.0):
+    """Time the FP64 oracle (as it stands) on the host cores on a bounded
+    sample: the full 2048^2 image of each PSF for a few iterations."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    px_it = 0
+    t_total = 0.0
+    per = []
+    for spec, f32 in inputs:
+        t = spec.dense()
+        psf = oracle.psf_dense(t, t.shape[1] // 2, t.shape[0] // 2)
+        f64 = f32.astype(np.float64)
+        its = 2
+        t0 = time.perf_counter()
+        oracle.rl(f64, psf, its)
+        dt = time.perf_counter() - t0
+        t_total += dt
+        px_it += f64.size * its
+        per.append(f"{spec.name}:{its}it/{dt:.1f}s")
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": px_it / t_total / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full 2048x2048 image, 2 iterations per PSF ({', '.join(per)}); "
+                      f"FP64 direct summation, OpenMP over rows"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    inputs = make_inputs()
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state worth the CPU time
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline_run(inputs)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    px_step = 3 * SIZE * SIZE * ITERS
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": px_step / (v * 1e6) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (CPU oracle, bounded sample)", "size": SIZE,
+                       "iterations": ITERS},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1304_7211_gb300 import _build, rl
+    _build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    inputs = make_inputs()
+    solves = []
+    for spec, f32 in inputs:
+        d = rl.Deconvolver(spec, device=local, stream=stream)
+        f_dev = torch.from_numpy(f32).to(dev)
+        u_dev = torch.empty_like(f_dev)
+        f_host = torch.from_numpy(f32).pin_memory()
+        u_host = torch.empty_like(f_host).pin_memory()
+        solves.append((spec, d, f_dev, u_dev, f_host, u_host))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step_device():
+        for spec, d, f, u, _, _ in solves:
+            rl.rl_iterate(d.ctx, f, None, u, SIZE, SIZE, SIZE, ITERS)
+
+    def step_host():
+        for spec, d, _, _, fh, uh in solves:
+            rl.rl_iterate(d.ctx, fh, None, uh, SIZE, SIZE, SIZE, ITERS)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # per-kernel timing of one solve of each PSF (same stream, CUDA events)
+    def solve_ms(idx, reps=3):
+        spec, d, f, u, _, _ = solves[idx]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            ev[0].record(stream)
+            rl.rl_iterate(d.ctx, f, None, u, SIZE, SIZE, SIZE, ITERS)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        return statistics.median(ts)
+
+    for _ in range(max(args.warmup, 3)):
+        step_device()
+    barrier()
+
+    clocks = Clocks(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between steps, outside the events
+        starts[i].record(stream)
+        step_device()
+        ends[i].record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    px_step = 3 * SIZE * SIZE * ITERS
+    value = ws * px_step * args.steps / (t_ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers
+    for _ in range(2):
+        step_host()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        step_host()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = ws * px_step * e2e_steps / e2e_s / 1e6
+    plane = SIZE * SIZE * 4
+
+    # dominant kernel: per-solve times, roofline of the slowest
+    per = {solves[i][0].name: solve_ms(i) for i in range(3)}
+    pk, pk_kind = peaks()
+    dom = max(per, key=per.get)
+    launch_ms = per[dom] / ITERS
+    px = SIZE * SIZE
+    if dom.startswith("disc"):
+        # span path: 2 (2r+1) additions per pixel per convolution (Sec. 3,
+        # generic box filter), two convolutions, plus ratio, update, scaling
+        r = 8
+        flops = px * (4 * (2 * r + 1) + 4)
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s, TFLOP/s (adds)
+        achieved = flops / (launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": f"k_tile<span> ({dom})",
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (adds)"}
+    else:
+        bytes_ = px * 12
+        achieved = bytes_ / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_source": pk_kind}
+    roof["per_solve_ms"] = per
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "size": SIZE, "iterations": ITERS,
+                       "psfs": [s[0].name for s in solves], "boundary": "mirror",
+                       "l2": "512 MiB write between steps, outside the timed events",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * plane,
+                    "d2h_bytes_per_step": 3 * plane},
+            "gpu_launches": 3 * ITERS * args.steps,
+            "roofline": roof, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_run(inputs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in solves:
+        s[1].close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

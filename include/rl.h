@@ -1,0 +1,204 @@
+/*
+ * rl.h -- C ABI of the GB300 (sm_103a) Richardson-Lucy deconvolution library.
+ *
+ * The library runs the hot path of non-blind Richardson-Lucy (RL)
+ * deconvolution as described by Welk & Erler, "Algorithmic Optimisations for
+ * Iterative Deconvolution Methods":
+ *
+ *   Sec. 1, Eq. 2   given the observed image f and the PSF h, find u with
+ *                   f ~ u (x) h;
+ *   Sec. 2, Eq. 3   u^{k+1} = ( h* (x) ( f / (u^k (x) h) ) ) . u^k,  u^0 = f,
+ *                   h* = h reflected about the origin; the iteration count
+ *                   is the only parameter of the method;
+ *   Sec. 2          missing pixels outside the image are continued from the
+ *                   image (clamp = closest pixel, or half-sample mirror);
+ *   Sec. 3          fast convolutions for special PSFs: a running-sum box
+ *                   filter for linear motion blur, the "generic box filter"
+ *                   (per-row spans) for uniform convex PSFs such as the
+ *                   defocus disc, and direct summation / the list filter for
+ *                   general PSFs;
+ *   Sec. 4, Eq. 4-5 selective convolution ("thinning"): pixels whose change
+ *                   falls below a threshold become inactive, keep their last
+ *                   re-blurred value v and stop changing; every P (= 10)
+ *                   iterations all pixels are active again.
+ *
+ * Conventions for every entry point:
+ *   - Return an rl_status; no call aborts the process and no C++ exception
+ *     crosses this boundary.  On failure rl_last_error(ctx) describes it.
+ *   - Images are single-channel, row-major (x fastest), with a row pitch
+ *     given in ELEMENTS.  The element type is the context's storage type
+ *     (float, bfloat16 or float16); arithmetic is FP32 in every mode.
+ *   - A context is used by one host thread at a time.  It owns all scratch
+ *     device memory it needs; scratch is allocated on first use, grows when a
+ *     larger image arrives, and is freed by rl_destroy.
+ *   - Work is issued on the context's CUDA stream (rl_config.stream; NULL =
+ *     the legacy default stream).  Calls return when the work is queued,
+ *     except where stated.
+ */
+#ifndef RL_GB300_H
+#define RL_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rl_ctx rl_ctx; /* opaque; created by rl_create */
+
+typedef enum {
+    RL_OK = 0,
+    RL_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad PSF, ...         */
+    RL_ERR_UNSUPPORTED = 2, /* valid request this build cannot run          */
+    RL_ERR_OOM = 3,         /* device or host allocation failed             */
+    RL_ERR_CUDA = 4,        /* a CUDA call failed (message has the reason)  */
+    RL_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                */
+    RL_ERR_STATE = 6        /* call out of order (e.g. no PSF set yet)      */
+} rl_status;
+
+typedef enum {
+    RL_PSF_MOTION = 0, /* uniform linear motion blur, Sec. 3 Fig. 1a          */
+    RL_PSF_DISC = 1,   /* uniform disc (defocus), Sec. 3 "Defocus blur"      */
+    RL_PSF_DENSE = 2   /* arbitrary non-negative taps, Sec. 3 "Sparse blur"  */
+} rl_psf_kind;
+
+typedef enum { RL_STORAGE_F32 = 0, RL_STORAGE_BF16 = 1, RL_STORAGE_F16 = 2 } rl_storage;
+
+typedef enum {
+    RL_BOUNDARY_MIRROR = 0, /* half-sample symmetric: ... c b a | a b c ...   */
+    RL_BOUNDARY_CLAMP = 1   /* closest image pixel (the paper's choice, Sec. 2) */
+} rl_boundary;
+
+typedef enum {
+    RL_PATH_AUTO = 0,    /* motion -> RUNSUM, disc -> SPAN, dense -> STENCIL     */
+    RL_PATH_RUNSUM = 1,  /* sliding-window box filter along x or y (motion only)  */
+    RL_PATH_SPAN = 2,    /* per-row span sums of a uniform PSF (motion, disc,
+                            or dense taps that are uniform with one contiguous
+                            run per row)                                         */
+    RL_PATH_STENCIL = 3  /* direct summation over the non-zero taps (any PSF)     */
+} rl_path;
+
+/*
+ * PSF descriptor (Sec. 3, Fig. 1).
+ *   RL_PSF_MOTION: `length` >= 1 pixels along `axis` (0 = x, 1 = y); taps
+ *       1/length at offsets [-(length/2), length-1-length/2].
+ *   RL_PSF_DISC:   `radius` >= 0; support dx^2 + dy^2 <= radius^2 (pixel-
+ *       centre inclusion), weight 1/|support|.
+ *   RL_PSF_DENSE:  `kw` x `kh` host array `taps` (row-major, taps[j*kw+i] at
+ *       offset (i - anchor_x, j - anchor_y)); anchor_x/anchor_y < 0 select the
+ *       centre (kw/2, kh/2).  Taps must be finite and >= 0 with a positive
+ *       sum; they are copied and normalised to unit sum.
+ * Offsets follow convolution: (u (x) h)(p) = sum_t h(t) u(p - t).
+ */
+typedef struct {
+    int kind;                /* rl_psf_kind                     */
+    int axis;                /* MOTION: 0 = x, 1 = y            */
+    int length;              /* MOTION                          */
+    int radius;              /* DISC                            */
+    int kw, kh;              /* DENSE                           */
+    int anchor_x, anchor_y;  /* DENSE; < 0 = centre             */
+    const float *taps;       /* DENSE; host memory, kw*kh items */
+} rl_psf_desc;
+
+/*
+ * Selective convolution (Sec. 4, Eq. 4-5).  Pass NULL to rl_iterate for
+ * plain RL.  Iteration k (counting from 0 in each rl_iterate call) is "full"
+ * when k % reset_period == 0: every pixel is used.  Otherwise only active
+ * pixels are re-blurred and updated; inactive pixels keep the ratio f/v of
+ * their last active iteration and do not change.  The change of a used pixel
+ * is |c - 1| (relative = 1, c = the correction factor, 0 where u = 0) or
+ * |u' - u| (relative = 0).  A pixel whose change is < threshold becomes
+ * inactive: after every iteration when update_period == 1 (Sec. 4), or only
+ * after full iterations when update_period == reset_period (the mask is then
+ * fixed for the rest of the epoch).
+ */
+typedef struct {
+    float threshold;   /* >= 0; 0 reproduces plain RL (Table 2, first row) */
+    int relative;      /* 1: |c - 1|, 0: |u' - u| (absolute, Sec. 4)         */
+    int reset_period;  /* P >= 1, the paper uses 10                        */
+    int update_period; /* 1 or reset_period                                */
+} rl_thinning;
+
+typedef struct {
+    int device;     /* CUDA device ordinal                                   */
+    void *stream;   /* cudaStream_t to issue work on; NULL = default stream */
+    int storage;    /* rl_storage of f, u0, u_out (and internal u buffers)  */
+    int boundary;   /* rl_boundary                                          */
+    int path;       /* rl_path                                              */
+} rl_config;
+
+typedef struct {
+    long long iterations;             /* iterations run                        */
+    long long pixel_iterations;       /* W * H * iterations                    */
+    long long active_pixel_iterations;/* pixel-iterations actually re-blurred  */
+    double device_ms;                 /* stream time of the call (CUDA events) */
+    int path;                         /* rl_path that ran                      */
+} rl_stats;
+
+/*
+ * Create a context on cfg->device.  cfg may be NULL (device 0, default
+ * stream, FP32, mirror boundary, AUTO path).  On success *out owns the
+ * context; release it with rl_destroy.  Errors: RL_ERR_INVALID_ARG for a null
+ * `out` or an unknown enum value, RL_ERR_UNSUPPORTED when the device is not a
+ * compute capability 10.3 GPU, RL_ERR_CUDA/RL_ERR_OOM when setup fails.
+ */
+rl_status rl_create(const rl_config *cfg, rl_ctx **out);
+
+/*
+ * Set the PSF h of Eq. 3 (descriptor semantics above).  Copies and
+ * normalises the taps, derives the per-row span table (Sec. 3, generic box
+ * filter) and uploads both to the device.  Errors: RL_ERR_INVALID_ARG for a
+ * bad descriptor (negative or non-finite taps, zero sum, length < 1,
+ * radius < 0, null taps, kw/kh < 1, anchor outside the array, more than
+ * 65536 taps); RL_ERR_UNSUPPORTED when the context's forced path cannot
+ * represent the PSF (RUNSUM needs a motion PSF; SPAN needs a uniform PSF with
+ * one contiguous run per row).
+ */
+rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *psf);
+
+/*
+ * Run `iterations` RL iterations (Eq. 3) of the current PSF on a W x H image.
+ *   f      observed image (read only).
+ *   u0     starting image; NULL means u0 = f (the paper's choice).
+ *   u_out  receives u^iterations; may alias u0 but not f.
+ *   pitch  row pitch in elements for f, u0 and u_out (>= W).
+ *   thin   NULL for plain RL, else selective convolution (see rl_thinning).
+ *   stats  NULL, or receives counters; a non-NULL stats makes the call wait
+ *          for the stream (active counts and timing are read back).
+ * Pointers may be device memory or host memory (pageable or pinned); host
+ * buffers are staged through library-owned device buffers with copies on the
+ * context stream, and the call then returns only after u_out is written.
+ * Device pointers must be on the context's device and aligned to the element
+ * size.  The boundary continuation is the context's.  The PSF's extent on
+ * each side must be smaller than the image along that axis.
+ * Errors: RL_ERR_INVALID_ARG (null f/u_out, W or H < 1, pitch < W,
+ * iterations < 0, u_out == f, PSF larger than the image, bad thinning
+ * parameters), RL_ERR_STATE (no PSF set), RL_ERR_OOM, RL_ERR_CUDA.
+ */
+rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void *u_out,
+                     int W, int H, long long pitch, int iterations,
+                     const rl_thinning *thin, rl_stats *stats);
+
+/*
+ * Diagnostics for selective convolution (Sec. 4): copy the active-pixel mask
+ * left by the last thinned rl_iterate on this context into dst, W x H bytes
+ * with a row pitch of dst_pitch bytes (host or device memory).  A byte is 1
+ * when the pixel would be re-blurred in the next (non-full) iteration.  Waits
+ * for the context stream.  Errors: RL_ERR_INVALID_ARG (null dst, pitch < W),
+ * RL_ERR_STATE (no thinned iteration has run on this context), RL_ERR_CUDA.
+ */
+rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch);
+
+/* Release the context and all device memory it owns.  NULL is a no-op. */
+rl_status rl_destroy(rl_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  With ctx == NULL, the
+ * message of the last failed rl_create on this thread.  The pointer stays
+ * valid until the next call on the same context. */
+const char *rl_last_error(const rl_ctx *ctx);
+
+/* Library version string, e.g. "rl-gb300 0.1 sm_103a". */
+const char *rl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RL_GB300_H */

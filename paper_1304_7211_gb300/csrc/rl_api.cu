@@ -1,0 +1,522 @@
+// rl_api.cu -- host runtime and C ABI of the RL library (declared in
+// include/rl.h).
+//
+// The runtime plans a PSF (dense taps, extents, per-row span table of Sec. 3's
+// generic box filter), owns the scratch device memory (ping-pong u buffers,
+// the selective-convolution mask and stale-ratio planes, host staging
+// buffers) and drives the fused iteration kernels on the context stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rl.h"
+#include "rl_launch.h"
+
+using rl::IterArgs;
+
+struct rl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int storage = RL_STORAGE_F32;
+    int boundary = RL_BOUNDARY_MIRROR;
+    int path_pref = RL_PATH_AUTO;
+    std::string err;
+
+    // PSF plan
+    bool has_psf = false;
+    int kind = 0, axis = 0;
+    int kw = 0, kh = 0, ax = 0, ay = 0;  // dense layout; bx = kw-1-ax, by = kh-1-ay
+    std::vector<float> taps;             // normalised, row-major kh x kw
+    bool uniform = false;                // one contiguous run of equal taps per row
+    std::vector<int2> spans;             // per row j: [lo, hi] offsets (lo > hi = empty)
+    float weight = 0.f;                  // the common tap value when uniform
+    float *d_taps = nullptr;
+    int2 *d_spans = nullptr;
+
+    // scratch
+    void *ubuf[2] = {nullptr, nullptr};
+    size_t ubuf_bytes = 0;
+    uint8_t *mask[2] = {nullptr, nullptr};
+    float *rstale = nullptr;
+    size_t thin_px = 0;
+    unsigned long long *d_counter = nullptr;
+    void *stage[3] = {nullptr, nullptr, nullptr};
+    size_t stage_bytes[3] = {0, 0, 0};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // mask left by the last thinned call (rl_get_mask)
+    const uint8_t *last_mask = nullptr;
+    int last_W = 0, last_H = 0;
+    long long last_mp = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+size_t elem_size(int storage) { return storage == RL_STORAGE_F32 ? 4 : 2; }
+
+rl_status fail(rl_ctx *c, rl_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+rl_status cuda_fail(rl_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? RL_ERR_OOM : RL_ERR_CUDA, m);
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+rl_status grow(rl_ctx *ctx, void **p, size_t *have, size_t need, const char *what) {
+    if (*have >= need && *p) return RL_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    CK(cudaMalloc(p, need), what);
+    *have = need;
+    return RL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rl_version(void) { return "rl-gb300 0.1 sm_103a"; }
+
+const char *rl_last_error(const rl_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "rl_create: out is NULL";
+        return RL_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    rl_config c = {0, nullptr, RL_STORAGE_F32, RL_BOUNDARY_MIRROR, RL_PATH_AUTO};
+    if (cfg) c = *cfg;
+    if (c.storage < RL_STORAGE_F32 || c.storage > RL_STORAGE_F16 ||
+        (c.boundary != RL_BOUNDARY_MIRROR && c.boundary != RL_BOUNDARY_CLAMP) ||
+        c.path < RL_PATH_AUTO || c.path > RL_PATH_STENCIL) {
+        g_create_error = "rl_create: unknown storage, boundary or path value";
+        return RL_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        (void)cudaGetLastError();
+        g_create_error = "rl_create: no such CUDA device";
+        return e == cudaSuccess ? RL_ERR_INVALID_ARG : RL_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c.device) != cudaSuccess) {
+        g_create_error = "rl_create: cudaGetDeviceProperties failed";
+        return RL_ERR_CUDA;
+    }
+    if (prop.major != 10 || prop.minor != 3) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "rl_create: device %d is sm_%d%d; this library is built for sm_103a",
+                 c.device, prop.major, prop.minor);
+        g_create_error = buf;
+        return RL_ERR_UNSUPPORTED;
+    }
+    rl_ctx *ctx = new (std::nothrow) rl_ctx;
+    if (!ctx) {
+        g_create_error = "rl_create: out of host memory";
+        return RL_ERR_OOM;
+    }
+    ctx->device = c.device;
+    ctx->stream = (cudaStream_t)c.stream;
+    ctx->storage = c.storage;
+    ctx->boundary = c.boundary;
+    ctx->path_pref = c.path;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("rl_create: ") + cudaGetErrorString(e);
+        (void)cudaGetLastError();
+        rl_destroy(ctx);
+        return RL_ERR_CUDA;
+    }
+    *out = ctx;
+    return RL_OK;
+}
+
+rl_status rl_destroy(rl_ctx *ctx) {
+    if (!ctx) return RL_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_taps);
+    cudaFree(ctx->d_spans);
+    cudaFree(ctx->ubuf[0]);
+    cudaFree(ctx->ubuf[1]);
+    cudaFree(ctx->mask[0]);
+    cudaFree(ctx->mask[1]);
+    cudaFree(ctx->rstale);
+    cudaFree(ctx->d_counter);
+    for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    cudaSetDevice(prev);
+    delete ctx;
+    return RL_OK;
+}
+
+rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
+    if (!ctx) return RL_ERR_INVALID_ARG;
+    if (!d) return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: descriptor is NULL");
+    std::vector<double> t;
+    int kw = 0, kh = 0, ax = 0, ay = 0;
+    if (d->kind == RL_PSF_MOTION) {
+        if (d->length < 1 || (d->axis != 0 && d->axis != 1))
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: motion needs length >= 1 and axis 0 or 1");
+        if (d->length > 65536) return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: motion length too large");
+        t.assign(d->length, 1.0);
+        kw = d->axis == 0 ? d->length : 1;
+        kh = d->axis == 0 ? 1 : d->length;
+        ax = kw / 2;
+        ay = kh / 2;
+    } else if (d->kind == RL_PSF_DISC) {
+        if (d->radius < 0 || d->radius > 127)
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: disc radius must be in [0, 127]");
+        const int r = d->radius;
+        kw = kh = 2 * r + 1;
+        ax = ay = r;
+        t.assign((size_t)kw * kh, 0.0);
+        for (int j = 0; j < kh; ++j)
+            for (int i = 0; i < kw; ++i) {
+                const long dx = i - r, dy = j - r;
+                t[(size_t)j * kw + i] = (dx * dx + dy * dy <= (long)r * r) ? 1.0 : 0.0;
+            }
+    } else if (d->kind == RL_PSF_DENSE) {
+        if (!d->taps || d->kw < 1 || d->kh < 1 || (long long)d->kw * d->kh > 65536)
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: dense taps need kw, kh >= 1, kw*kh <= 65536 and a taps array");
+        kw = d->kw;
+        kh = d->kh;
+        ax = d->anchor_x < 0 ? kw / 2 : d->anchor_x;
+        ay = d->anchor_y < 0 ? kh / 2 : d->anchor_y;
+        if (ax >= kw || ay >= kh)
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: anchor outside the tap array");
+        t.resize((size_t)kw * kh);
+        for (size_t k = 0; k < t.size(); ++k) t[k] = d->taps[k];
+    } else {
+        return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: unknown PSF kind");
+    }
+    double sum = 0.0;
+    for (double v : t) {
+        if (!std::isfinite(v) || v < 0.0)
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: taps must be finite and >= 0");
+        sum += v;
+    }
+    if (!(sum > 0.0) || !std::isfinite(sum))
+        return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: taps must have a positive sum");
+
+    // Span table (Sec. 3, generic box filter): uniform taps with one
+    // contiguous run per row.
+    bool uniform = true;
+    double common = -1.0;
+    std::vector<int2> spans(kh);
+    for (int j = 0; j < kh; ++j) {
+        int first = -1, last = -1;
+        for (int i = 0; i < kw; ++i) {
+            const double v = t[(size_t)j * kw + i];
+            if (v != 0.0) {
+                if (first < 0) first = i;
+                else if (last != i - 1) uniform = false;
+                last = i;
+                if (common < 0.0) common = v;
+                else if (v != common) uniform = false;
+            }
+        }
+        spans[j] = first < 0 ? make_int2(1, 0) : make_int2(first - ax, last - ax);
+    }
+    const int want = ctx->path_pref;
+    if (want == RL_PATH_RUNSUM && d->kind != RL_PSF_MOTION)
+        return fail(ctx, RL_ERR_UNSUPPORTED, "rl_set_psf: the running-sum path needs a motion PSF");
+    if (want == RL_PATH_SPAN && !uniform)
+        return fail(ctx, RL_ERR_UNSUPPORTED,
+                    "rl_set_psf: the span path needs equal taps in one contiguous run per row");
+
+    std::vector<float> tf(t.size());
+    for (size_t k = 0; k < t.size(); ++k) tf[k] = (float)(t[k] / sum);
+
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_taps);
+    cudaFree(ctx->d_spans);
+    ctx->d_taps = nullptr;
+    ctx->d_spans = nullptr;
+    ctx->has_psf = false;
+    cudaError_t e = cudaMalloc(&ctx->d_taps, tf.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_spans, spans.size() * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->d_taps, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->d_spans, spans.data(), spans.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_set_psf: upload");
+
+    ctx->kind = d->kind;
+    ctx->axis = d->kind == RL_PSF_MOTION ? d->axis : 0;
+    ctx->kw = kw;
+    ctx->kh = kh;
+    ctx->ax = ax;
+    ctx->ay = ay;
+    ctx->taps = tf;
+    ctx->uniform = uniform;
+    ctx->spans = spans;
+    ctx->weight = uniform ? (float)(common / sum) : 0.f;
+    ctx->has_psf = true;
+    ctx->err.clear();
+    return RL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int choose_path(const rl_ctx *ctx, int W) {
+    const int L = ctx->kind == RL_PSF_MOTION ? (ctx->axis == 0 ? ctx->kw : ctx->kh) : 0;
+    int p = ctx->path_pref;
+    if (p == RL_PATH_AUTO) {
+        if (ctx->kind == RL_PSF_MOTION) p = RL_PATH_RUNSUM;
+        else if (ctx->uniform) p = RL_PATH_SPAN;
+        else p = RL_PATH_STENCIL;
+    }
+    // Rows too long for shared memory fall back to the span tile kernel.
+    if (p == RL_PATH_RUNSUM && ctx->axis == 0 && !rl::motion_x_fits(W, L)) p = RL_PATH_SPAN;
+    return p;
+}
+
+rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W, int H,
+                     long long pitch, int K, const rl_thinning *thin, int *path_out) {
+    const size_t es = elem_size(ctx->storage);
+    const int path = choose_path(ctx, W);
+    *path_out = path;
+    const void *start = u0 ? u0 : f;
+    if (K == 0) {
+        if (u_out != start)
+            CK(cudaMemcpy2DAsync(u_out, pitch * es, start, pitch * es, W * es, H,
+                                 cudaMemcpyDeviceToDevice, ctx->stream),
+               "rl_iterate: copy");
+        return RL_OK;
+    }
+    const long long sp = ((long long)W + 63) / 64 * 64;  // scratch pitch (elements)
+    const size_t plane = (size_t)sp * H;
+    if ((K > 1 || u_out == start) && ctx->ubuf_bytes < plane * es) {
+        cudaFree(ctx->ubuf[0]);
+        cudaFree(ctx->ubuf[1]);
+        ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
+        ctx->ubuf_bytes = 0;
+        CK(cudaMalloc(&ctx->ubuf[0], plane * es), "rl_iterate: scratch u");
+        CK(cudaMalloc(&ctx->ubuf[1], plane * es), "rl_iterate: scratch u");
+        ctx->ubuf_bytes = plane * es;
+    }
+    if (thin) {
+        if (ctx->thin_px < plane) {
+            for (int i = 0; i < 2; ++i) {
+                cudaFree(ctx->mask[i]);
+                ctx->mask[i] = nullptr;
+            }
+            cudaFree(ctx->rstale);
+            ctx->rstale = nullptr;
+            ctx->thin_px = 0;
+            ctx->last_mask = nullptr;
+            CK(cudaMalloc(&ctx->mask[0], plane), "rl_iterate: mask");
+            CK(cudaMalloc(&ctx->mask[1], plane), "rl_iterate: mask");
+            CK(cudaMalloc(&ctx->rstale, plane * sizeof(float)), "rl_iterate: stale ratio");
+            ctx->thin_px = plane;
+        }
+        CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream),
+           "rl_iterate: counter");
+    }
+
+    IterArgs a;
+    memset(&a, 0, sizeof a);
+    a.f = f;
+    a.W = W;
+    a.H = H;
+    a.f_pitch = pitch;
+    a.clamp = ctx->boundary == RL_BOUNDARY_CLAMP;
+    a.ax = ctx->ax;
+    a.bx = ctx->kw - 1 - ctx->ax;
+    a.ay = ctx->ay;
+    a.by = ctx->kh - 1 - ctx->ay;
+    a.weight = ctx->weight;
+    a.taps = ctx->d_taps;
+    a.spans = ctx->d_spans;
+    a.m_pitch = sp;
+    a.rstale = ctx->rstale;
+    a.active_count = thin ? ctx->d_counter : nullptr;
+    if (thin) {
+        a.relative = thin->relative != 0;
+        a.tau = thin->threshold;
+    }
+    const rl::TileShape ts = rl::tile_shape_for(a.ax, a.bx, a.ay, a.by);
+    int cur = 0;  // mask plane holding the current mask
+    for (int k = 0; k < K; ++k) {
+        const bool last = k == K - 1;
+        a.u_in = k == 0 ? start : ctx->ubuf[(k - 1) & 1];
+        a.in_pitch = k == 0 ? pitch : sp;
+        const bool direct = last && !(k == 0 && u_out == start);
+        a.u_out = direct ? u_out : ctx->ubuf[k & 1];
+        a.out_pitch = direct ? pitch : sp;
+        if (thin) {
+            a.full = (k % thin->reset_period) == 0;
+            a.update_mask = thin->update_period == 1 || a.full;
+            a.mask_in = ctx->mask[cur];
+            a.mask_out = ctx->mask[cur ^ 1];
+        }
+        cudaError_t e;
+        if (path == RL_PATH_RUNSUM)
+            e = ctx->axis == 0 ? rl::launch_motion_x(a, ctx->storage, thin != nullptr, ctx->stream)
+                               : rl::launch_motion_y(a, ctx->storage, thin != nullptr, ctx->stream);
+        else
+            e = rl::launch_tile(a, ctx->storage, thin != nullptr,
+                                path == RL_PATH_SPAN ? rl::TILE_SPAN : rl::TILE_STENCIL, ts, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
+        if (thin && a.update_mask) cur ^= 1;
+        if (thin) {
+            ctx->last_mask = ctx->mask[cur];
+            ctx->last_W = W;
+            ctx->last_H = H;
+            ctx->last_mp = sp;
+        }
+        if (last && !direct)
+            CK(cudaMemcpy2DAsync(u_out, pitch * es, a.u_out, sp * es, W * es, H,
+                                 cudaMemcpyDeviceToDevice, ctx->stream),
+               "rl_iterate: copy out");
+    }
+    return RL_OK;
+}
+
+}  // namespace
+
+extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W,
+                                int H, long long pitch, int iterations, const rl_thinning *thin,
+                                rl_stats *stats) {
+    if (!ctx) return RL_ERR_INVALID_ARG;
+    if (!f || !u_out) return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate: f and u_out must not be NULL");
+    if (W < 1 || H < 1 || pitch < W || iterations < 0)
+        return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate: need W, H >= 1, pitch >= W, iterations >= 0");
+    if (u_out == f) return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate: u_out must not alias f");
+    if (!ctx->has_psf) return fail(ctx, RL_ERR_STATE, "rl_iterate: no PSF set");
+    const int bx = ctx->kw - 1 - ctx->ax, by = ctx->kh - 1 - ctx->ay;
+    if (ctx->ax >= W || bx >= W || ctx->ay >= H || by >= H)
+        return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate: PSF extent must be smaller than the image");
+    if (thin) {
+        if (!(thin->threshold >= 0.f) || thin->reset_period < 1 ||
+            (thin->update_period != 1 && thin->update_period != thin->reset_period))
+            return fail(ctx, RL_ERR_INVALID_ARG,
+                        "rl_iterate: thinning needs threshold >= 0, reset_period >= 1, "
+                        "update_period 1 or reset_period");
+    }
+    const size_t es = elem_size(ctx->storage);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    struct Restore {
+        int d, p;
+        ~Restore() { if (d != p) cudaSetDevice(p); }
+    } restore{ctx->device, prev};
+
+    const bool dev_f = is_device_ptr(f), dev_o = is_device_ptr(u_out);
+    const bool dev_u = u0 ? is_device_ptr(u0) : true;
+    const bool staged = !(dev_f && dev_o && dev_u);
+    const void *df = f, *du = u0;
+    void *dout = u_out;
+    long long dp = pitch;
+    if (staged) {
+        // Any host buffer: stage every input into library-owned device
+        // buffers with a packed pitch, run there, and copy the result back.
+        dp = W;
+        const size_t bytes = (size_t)W * H * es;
+        const void *src[2] = {f, u0};
+        const bool on_dev[2] = {dev_f, dev_u};
+        for (int i = 0; i < 3; ++i) {
+            if (i == 1 && !u0) continue;
+            rl_status st = grow(ctx, &ctx->stage[i], &ctx->stage_bytes[i], bytes, "rl_iterate: staging");
+            if (st != RL_OK) return st;
+            if (i < 2)
+                CK(cudaMemcpy2DAsync(ctx->stage[i], W * es, src[i], pitch * es, W * es, H,
+                                     on_dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     ctx->stream),
+                   "rl_iterate: upload");
+        }
+        df = ctx->stage[0];
+        du = u0 ? ctx->stage[1] : nullptr;
+        dout = ctx->stage[2];
+    }
+    if (stats) CK(cudaEventRecord(ctx->ev0, ctx->stream), "rl_iterate: event");
+    int path = 0;
+    rl_status st = run_device(ctx, df, du, dout, W, H, dp, iterations, thin, &path);
+    if (st != RL_OK) return st;
+    if (staged) {
+        CK(cudaMemcpy2DAsync(u_out, pitch * es, dout, W * es, W * es, H,
+                             dev_o ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+           "rl_iterate: download");
+    }
+    if (stats) {
+        CK(cudaEventRecord(ctx->ev1, ctx->stream), "rl_iterate: event");
+        CK(cudaEventSynchronize(ctx->ev1), "rl_iterate: sync");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "rl_iterate: timing");
+        unsigned long long act = (unsigned long long)W * H * iterations;
+        if (thin) CK(cudaMemcpy(&act, ctx->d_counter, sizeof act, cudaMemcpyDeviceToHost), "rl_iterate: counter");
+        stats->iterations = iterations;
+        stats->pixel_iterations = (long long)W * H * iterations;
+        stats->active_pixel_iterations = (long long)act;
+        stats->device_ms = ms;
+        stats->path = path;
+    } else if (staged) {
+        CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: sync");
+    }
+    CK(cudaGetLastError(), "rl_iterate");
+    ctx->err.clear();
+    return RL_OK;
+}
+
+extern "C" rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch) {
+    if (!ctx) return RL_ERR_INVALID_ARG;
+    if (!dst) return fail(ctx, RL_ERR_INVALID_ARG, "rl_get_mask: dst is NULL");
+    if (!ctx->last_mask) return fail(ctx, RL_ERR_STATE, "rl_get_mask: no thinned iteration has run");
+    if (dst_pitch < ctx->last_W) return fail(ctx, RL_ERR_INVALID_ARG, "rl_get_mask: dst_pitch < W");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpy2DAsync(dst, dst_pitch, ctx->last_mask, ctx->last_mp, ctx->last_W,
+                                      ctx->last_H, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_get_mask");
+    return RL_OK;
+}

@@ -1,0 +1,96 @@
+// rl_common.cuh -- device-side building blocks shared by the RL kernels.
+//
+// Storage types, the boundary index map of Sec. 2, and the argument block of
+// one fused RL iteration (Eq. 3, with the selective-convolution state of
+// Eq. 4-5).  Every kernel computes in FP32 whatever the storage type.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rl {
+
+// ---- storage ---------------------------------------------------------------
+template <typename T> struct Stor;
+template <> struct Stor<float> {
+    static __device__ __forceinline__ float ld(const float *p, long long i) { return __ldg(p + i); }
+    static __device__ __forceinline__ float ldc(const float *p, long long i) { return p[i]; }
+    static __device__ __forceinline__ void st(float *p, long long i, float v) { p[i] = v; }
+};
+template <> struct Stor<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, long long i) { return __bfloat162float(__ldg(p + i)); }
+    static __device__ __forceinline__ float ldc(const __nv_bfloat16 *p, long long i) { return __bfloat162float(p[i]); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
+};
+template <> struct Stor<__half> {
+    static __device__ __forceinline__ float ld(const __half *p, long long i) { return __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ float ldc(const __half *p, long long i) { return __half2float(p[i]); }
+    static __device__ __forceinline__ void st(__half *p, long long i, float v) { p[i] = __float2half_rn(v); }
+};
+
+// ---- boundary continuation (Sec. 2) ----------------------------------------
+// clamp = closest image pixel; mirror = half-sample symmetric, 2n-periodic.
+__device__ __forceinline__ int bmap(int e, int n, int clamp) {
+    if (e >= 0 && e < n) return e;
+    if (clamp) return e < 0 ? 0 : n - 1;
+    int period = 2 * n;
+    int r = e % period;
+    if (r < 0) r += period;
+    return r < n ? r : period - 1 - r;
+}
+
+// ---- one fused iteration ----------------------------------------------------
+// The PSF support lies in offsets t in [-ax, bx] x [-ay, by]:
+//   forward  v(p) = sum_t h(t) u(m(p - t))          (reads [p-b, p+a])
+//   adjoint  c(p) = sum_t h(t) q(m(p + t))          (reads [p-a, p+b])
+// i.e. the pad-flip reading of h* in Eq. 3 (same continuation m for both).
+struct IterArgs {
+    const void *f;
+    const void *u_in;
+    void *u_out;
+    int W, H;
+    long long f_pitch, in_pitch, out_pitch;  // elements
+    int clamp;                               // 1 = clamp, 0 = mirror
+    int ax, bx, ay, by;                      // PSF extents
+    float weight;                            // uniform weight (RUNSUM, SPAN)
+    const float *taps;                       // STENCIL: dense (ay+by+1) x (ax+bx+1)
+    const int2 *spans;                       // SPAN: per PSF row j (ty = j - ay): [lo, hi] of tx
+    // selective convolution (Eq. 4-5)
+    const uint8_t *mask_in;                  // 1 = active; read when !full
+    uint8_t *mask_out;                       // written when update_mask
+    float *rstale;                           // f/v of the last active iteration
+    long long m_pitch;                       // pitch of mask and rstale planes
+    int full;                                // every pixel used this iteration
+    int update_mask;                         // write mask_out
+    int relative;                            // |c-1| (1) or |u'-u| (0)
+    float tau;                               // threshold (strict < -> inactive)
+    unsigned long long *active_count;        // += used pixels (nullable)
+};
+
+// Ratio f / v of Eq. 3 with q = 0 where the re-blurred value vanishes.
+__device__ __forceinline__ float rl_ratio(float f, float v) { return v > 0.f ? f / v : 0.f; }
+
+// Per-pixel selective-convolution bookkeeping at an output pixel p (Eq. 4-5).
+// Returns u'(p).  `use` says whether p was used this iteration, q is its
+// ratio (fresh when used).
+__device__ __forceinline__ float thin_update(const IterArgs &a, long long mi, bool use, float u,
+                                             float c, float q) {
+    float un = use ? u * c : u;
+    if (a.update_mask) {
+        float d = 0.f;
+        if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
+        bool keep = use && (d >= a.tau);
+        a.mask_out[mi] = (uint8_t)keep;
+        if (use && !keep) a.rstale[mi] = q;
+    }
+    return un;
+}
+
+__device__ __forceinline__ void count_active(unsigned long long *ctr, bool use) {
+    unsigned b = __ballot_sync(0xffffffffu, use);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(ctr, (unsigned long long)__popc(b));
+}
+
+}  // namespace rl

@@ -1,0 +1,256 @@
+"""ctypes binding of the C ABI declared in ``include/rl.h``.
+
+Argument marshalling only: every step of the Richardson-Lucy iteration runs in
+the CUDA kernels of ``librl_gb300.so``.  The functions keep the C names
+(``rl_create``, ``rl_set_psf``, ``rl_iterate``, ``rl_destroy``,
+``rl_last_error``).  Buffers may be passed as raw integer addresses, torch
+tensors (device or host) or numpy arrays (host); PyTorch is used only for
+device memory and the CUDA stream handle.
+
+There is no fallback: if the shared library is missing this module raises,
+and the library itself refuses to run on anything but an sm_103 GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librl_gb300.so")
+
+RL_OK, RL_ERR_INVALID_ARG, RL_ERR_UNSUPPORTED, RL_ERR_OOM, RL_ERR_CUDA, \
+    RL_ERR_TIMEOUT, RL_ERR_STATE = range(7)
+RL_PSF_MOTION, RL_PSF_DISC, RL_PSF_DENSE = range(3)
+RL_STORAGE_F32, RL_STORAGE_BF16, RL_STORAGE_F16 = range(3)
+RL_BOUNDARY_MIRROR, RL_BOUNDARY_CLAMP = range(2)
+RL_PATH_AUTO, RL_PATH_RUNSUM, RL_PATH_SPAN, RL_PATH_STENCIL = range(4)
+
+STORAGE = {"f32": RL_STORAGE_F32, "bf16": RL_STORAGE_BF16, "f16": RL_STORAGE_F16}
+BOUNDARY = {"mirror": RL_BOUNDARY_MIRROR, "clamp": RL_BOUNDARY_CLAMP}
+PATH = {"auto": RL_PATH_AUTO, "runsum": RL_PATH_RUNSUM, "span": RL_PATH_SPAN,
+        "stencil": RL_PATH_STENCIL}
+PATH_NAME = {v: k for k, v in PATH.items()}
+STATUS_NAME = {RL_OK: "RL_OK", RL_ERR_INVALID_ARG: "RL_ERR_INVALID_ARG",
+               RL_ERR_UNSUPPORTED: "RL_ERR_UNSUPPORTED", RL_ERR_OOM: "RL_ERR_OOM",
+               RL_ERR_CUDA: "RL_ERR_CUDA", RL_ERR_TIMEOUT: "RL_ERR_TIMEOUT",
+               RL_ERR_STATE: "RL_ERR_STATE"}
+
+
+class rl_psf_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("axis", ctypes.c_int), ("length", ctypes.c_int),
+                ("radius", ctypes.c_int), ("kw", ctypes.c_int), ("kh", ctypes.c_int),
+                ("anchor_x", ctypes.c_int), ("anchor_y", ctypes.c_int),
+                ("taps", ctypes.POINTER(ctypes.c_float))]
+
+
+class rl_thinning(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_float), ("relative", ctypes.c_int),
+                ("reset_period", ctypes.c_int), ("update_period", ctypes.c_int)]
+
+
+class rl_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("storage", ctypes.c_int), ("boundary", ctypes.c_int), ("path", ctypes.c_int)]
+
+
+class rl_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_longlong), ("pixel_iterations", ctypes.c_longlong),
+                ("active_pixel_iterations", ctypes.c_longlong), ("device_ms", ctypes.c_double),
+                ("path", ctypes.c_int)]
+
+
+class RLError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAME.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_lib = None
+
+# Every symbol include/rl.h declares.
+EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error", "rl_version",
+           "rl_get_mask")
+
+
+def load() -> ctypes.CDLL:
+    """Load ``librl_gb300.so`` (build it first with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.rl_create.restype = ctypes.c_int
+    lib.rl_create.argtypes = [ctypes.POINTER(rl_config), ctypes.POINTER(P)]
+    lib.rl_set_psf.restype = ctypes.c_int
+    lib.rl_set_psf.argtypes = [P, ctypes.POINTER(rl_psf_desc)]
+    lib.rl_iterate.restype = ctypes.c_int
+    lib.rl_iterate.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                               ctypes.c_int, ctypes.POINTER(rl_thinning), ctypes.POINTER(rl_stats)]
+    lib.rl_destroy.restype = ctypes.c_int
+    lib.rl_destroy.argtypes = [P]
+    lib.rl_last_error.restype = ctypes.c_char_p
+    lib.rl_last_error.argtypes = [P]
+    lib.rl_version.restype = ctypes.c_char_p
+    lib.rl_version.argtypes = []
+    lib.rl_get_mask.restype = ctypes.c_int
+    lib.rl_get_mask.argtypes = [P, P, ctypes.c_longlong]
+    _lib = lib
+    return lib
+
+
+def rl_last_error(ctx) -> str:
+    return load().rl_last_error(ctx).decode()
+
+
+def _check(rc: int, ctx) -> None:
+    if rc != RL_OK:
+        raise RLError(rc, rl_last_error(ctx))
+
+
+def rl_create(device: int = 0, stream=None, storage="f32", boundary="mirror", path="auto"):
+    """Create a context; ``stream`` is a ``cudaStream_t`` as int, a
+    ``torch.cuda.Stream`` or None (default stream)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    cfg = rl_config(device, stream or None, STORAGE.get(storage, storage),
+                    BOUNDARY.get(boundary, boundary), PATH.get(path, path))
+    h = ctypes.c_void_p()
+    rc = load().rl_create(ctypes.byref(cfg), ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
+def psf_desc(spec) -> tuple[rl_psf_desc, object]:
+    """Descriptor from a PSF spec with attributes kind/axis/length/radius/
+    taps/kw/kh (e.g. ``synth.PsfSpec``).  Returns (desc, keepalive)."""
+    kind = {"motion": RL_PSF_MOTION, "disc": RL_PSF_DISC, "dense": RL_PSF_DENSE}[spec.kind]
+    keep = None
+    taps = None
+    kw = kh = 0
+    if kind == RL_PSF_DENSE:
+        keep = (ctypes.c_float * len(spec.taps))(*spec.taps)
+        taps = ctypes.cast(keep, ctypes.POINTER(ctypes.c_float))
+        kw, kh = spec.kw, spec.kh
+    ax = getattr(spec, "anchor_x", -1)
+    ay = getattr(spec, "anchor_y", -1)
+    d = rl_psf_desc(kind, getattr(spec, "axis", 0), getattr(spec, "length", 0),
+                    getattr(spec, "radius", 0), kw, kh, ax, ay, taps)
+    return d, keep
+
+
+def rl_set_psf(ctx, spec_or_desc) -> None:
+    if isinstance(spec_or_desc, rl_psf_desc):
+        d, keep = spec_or_desc, None
+    else:
+        d, keep = psf_desc(spec_or_desc)
+    _check(load().rl_set_psf(ctx, ctypes.byref(d)), ctx)
+    del keep
+
+
+def _addr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):          # torch tensor
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):            # numpy array
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def rl_iterate(ctx, f, u0, u_out, W: int, H: int, pitch: int, iterations: int,
+               thinning: rl_thinning | None = None, stats: bool = False):
+    """Run RL iterations; returns an ``rl_stats`` when ``stats`` is true."""
+    st = rl_stats() if stats else None
+    rc = load().rl_iterate(ctx, _addr(f), _addr(u0), _addr(u_out), W, H, pitch, iterations,
+                           ctypes.byref(thinning) if thinning is not None else None,
+                           ctypes.byref(st) if st is not None else None)
+    _check(rc, ctx)
+    return st
+
+
+def rl_get_mask(ctx, dst, dst_pitch: int) -> None:
+    """Copy the active mask left by the last thinned rl_iterate into dst."""
+    _check(load().rl_get_mask(ctx, _addr(dst), dst_pitch), ctx)
+
+
+def rl_destroy(ctx) -> None:
+    if ctx:
+        load().rl_destroy(ctx)
+
+
+def thinning(threshold: float, relative: bool = True, reset_period: int = 10,
+             update_period: int = 1) -> rl_thinning:
+    return rl_thinning(float(threshold), int(bool(relative)), int(reset_period),
+                       int(update_period))
+
+
+class Deconvolver:
+    """Owns one context and one PSF; runs RL on torch tensors or numpy arrays.
+
+    ``run(f, iterations)`` with a CUDA tensor returns a CUDA tensor (work is
+    issued on the current torch stream); with a numpy array or CPU tensor the
+    library stages the data itself and the result comes back on the host.
+    """
+
+    def __init__(self, spec, device: int = 0, storage="f32", boundary="mirror",
+                 path="auto", stream=None):
+        self.device = device
+        self.storage = storage
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:  # pragma: no cover - torch is optional here
+                stream = None
+        self.ctx = rl_create(device, stream, storage, boundary, path)
+        rl_set_psf(self.ctx, spec)
+
+    def close(self):
+        if self.ctx:
+            rl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def mask(self):
+        """Active mask (uint8 numpy array) left by the last thinned run."""
+        import numpy as np
+        m = np.zeros((self._last_hw[0], self._last_hw[1]), np.uint8)
+        rl_get_mask(self.ctx, m, m.shape[1])
+        return m
+
+    def run(self, f, iterations: int, u0=None, out=None, thin: rl_thinning | None = None,
+            stats: bool = False):
+        H, W = f.shape[-2], f.shape[-1]
+        self._last_hw = (H, W)
+        if hasattr(f, "stride") and callable(f.stride):
+            pitch = f.stride(-2)
+        else:
+            if not f.flags["C_CONTIGUOUS"]:
+                raise ValueError("numpy inputs must be C-contiguous")
+            pitch = W
+        if out is None:
+            if hasattr(f, "new_empty"):
+                out = f.new_empty(f.shape)
+            else:
+                import numpy as np
+                out = np.empty_like(f)
+        st = rl_iterate(self.ctx, f, u0, out, W, H, pitch, iterations, thin, stats)
+        return (out, st) if stats else out

@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar (FP32 storage): relative L-inf error <= 1e-4 against the oracle after 50
+iterations, on seeded synthetic inputs at sizes that span several tiles with
+ragged tails.  Cross-path agreement (running sum / span / stencil) uses the
+same bound.  Thinned runs compare images within a bound derived from the
+threshold and masks by the count of disagreeing pixels.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1304_7211_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1304_7211_gb300 import _build, rl
+    _build.build()
+    return rl.load()
+
+
+def oracle_psf(spec):
+    t = spec.dense()
+    return oracle.psf_dense(t, t.shape[1] // 2, t.shape[0] // 2)
+
+
+def gpu_rl(spec, f32, iters, path="auto", boundary="mirror", storage="f32", thin=None,
+           u0=None, want_mask=False):
+    from paper_1304_7211_gb300 import rl
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[storage]
+    f = torch.from_numpy(f32).cuda().to(dt)
+    u0t = None if u0 is None else torch.from_numpy(u0).cuda().to(dt)
+    with rl.Deconvolver(spec, device=0, storage=storage, boundary=boundary, path=path) as d:
+        u, st = d.run(f, iters, u0=u0t, thin=thin, stats=True)
+        mask = d.mask() if (want_mask and thin is not None) else None
+    torch.cuda.synchronize()
+    out = u.float().cpu().numpy().astype(np.float64)
+    return (out, st, mask) if want_mask else (out, st)
+
+
+def case(w, h, spec, noise="poisson", seed=synth.SEED_BASE + 50):
+    c = synth.make_case(w, h, spec, 0, noise, seed)
+    return c.f.astype(np.float32)
+
+
+PATH_CASES = [
+    (synth.motion(15, 0), "runsum"), (synth.motion(31, 0), "runsum"),
+    (synth.motion(6, 0), "runsum"), (synth.motion(31, 1), "runsum"),
+    (synth.motion(8, 1), "runsum"), (synth.disc(3), "span"), (synth.disc(8), "span"),
+    (synth.motion(9, 0), "span"), (synth.motion(9, 1), "span"),
+    (synth.gaussian(7, 1.5), "stencil"), (synth.disc(4), "stencil"),
+    (synth.motion(11, 1), "stencil"),
+]
+
+
+@pytest.mark.parametrize("boundary", ["mirror", "clamp"])
+@pytest.mark.parametrize("spec,path", PATH_CASES, ids=lambda v: getattr(v, "name", v))
+def test_path_matches_oracle(spec, path, boundary):
+    # 203 x 301: ragged against every tile width; > 256 rows for the y strips.
+    f32 = case(203, 301, spec)
+    u, st = gpu_rl(spec, f32, 50, path=path, boundary=boundary)
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 50, boundary=boundary).u
+    err = oracle.rel_linf(u, ref)
+    assert err <= TOL, err
+    assert st.path == {"runsum": 1, "span": 2, "stencil": 3}[path]
+
+
+def test_asymmetric_dense_psf_off_centre_anchor():
+    rng = np.random.default_rng(3)
+    taps = rng.uniform(0.1, 1.0, size=(3, 5))
+    spec = synth.PsfSpec("dense", taps=tuple(taps.reshape(-1)), kw=5, kh=3)
+    spec_anchor = type("S", (), dict(kind="dense", taps=spec.taps, kw=5, kh=3,
+                                     anchor_x=4, anchor_y=0, axis=0, length=0, radius=0))()
+    f32 = case(130, 97, synth.gaussian(5, 1.0))
+    for boundary in ("mirror", "clamp"):
+        u, _ = gpu_rl(spec_anchor, f32, 30, path="stencil", boundary=boundary)
+        psf = oracle.psf_dense(taps, 4, 0)
+        ref = oracle.rl(f32.astype(np.float64), psf, 30, boundary=boundary).u
+        assert oracle.rel_linf(u, ref) <= TOL
+
+
+def test_uniform_rectangle_from_dense_taps_uses_span_path():
+    spec = synth.dense(np.ones((3, 5)))
+    f32 = case(150, 90, spec)
+    u, st = gpu_rl(spec, f32, 40)
+    assert st.path == 2
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 40).u
+    assert oracle.rel_linf(u, ref) <= TOL
+
+
+@pytest.mark.parametrize("spec,paths", [(synth.motion(31, 0), ("runsum", "span", "stencil")),
+                                        (synth.motion(31, 1), ("runsum", "span", "stencil")),
+                                        (synth.disc(8), ("span", "stencil"))],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_cross_path_agreement(spec, paths):
+    f32 = case(257, 263, spec, seed=synth.SEED_BASE + 51)
+    outs = [gpu_rl(spec, f32, 50, path=p)[0] for p in paths]
+    for o in outs[1:]:
+        assert oracle.rel_linf(o, outs[0]) <= TOL
+
+
+@pytest.mark.parametrize("spec", [synth.motion(5, 0), synth.motion(5, 1), synth.disc(1),
+                                  synth.gaussian(3, 0.8)], ids=lambda s: s.name)
+@pytest.mark.parametrize("shape", [(1, 7), (7, 1), (6, 6), (3, 40), (65, 2), (17, 33)])
+def test_small_and_degenerate_shapes(spec, shape):
+    H, W = shape
+    t = spec.dense()
+    if t.shape[1] // 2 >= W or t.shape[0] // 2 >= H:
+        pytest.skip("PSF larger than the image")
+    rng = np.random.default_rng(H * 100 + W)
+    f32 = rng.uniform(5, 250, size=(H, W)).astype(np.float32)
+    u, _ = gpu_rl(spec, f32, 12)
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 12).u
+    assert oracle.rel_linf(u, ref) <= TOL
+
+
+def test_delta_psf_and_zero_iterations():
+    f32 = case(70, 50, synth.motion(1, 0))
+    u, _ = gpu_rl(synth.motion(1, 0), f32, 5)
+    np.testing.assert_allclose(u, f32, rtol=1e-6)
+    u0 = np.full_like(f32, 3.0)
+    u, _ = gpu_rl(synth.disc(2), f32, 0, u0=u0)
+    np.testing.assert_array_equal(u, u0)
+
+
+def test_explicit_u0_and_aliasing_and_pitch():
+    from paper_1304_7211_gb300 import rl
+    spec = synth.disc(3)
+    f32 = case(120, 77, spec)
+    u0 = (f32 * 0.5 + 10).astype(np.float32)
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 7,
+                    u0=u0.astype(np.float64)).u
+    # pitched buffers: rows of 128 elements
+    fpad = torch.zeros((77, 128), device="cuda")
+    fpad[:, :120] = torch.from_numpy(f32).cuda()
+    upad = torch.zeros((77, 128), device="cuda")
+    upad[:, :120] = torch.from_numpy(u0).cuda()
+    with rl.Deconvolver(spec) as d:
+        for iters in (1, 7):
+            buf = upad.clone()
+            rl.rl_iterate(d.ctx, fpad, buf, buf, 120, 77, 128, iters)  # u_out aliases u0
+            torch.cuda.synchronize()
+            if iters == 7:
+                err = oracle.rel_linf(buf[:, :120].cpu().numpy(), ref)
+                assert err <= TOL
+            assert torch.all(buf[:, 120:] == 0)  # padding untouched
+
+
+def test_host_buffers_are_staged():
+    from paper_1304_7211_gb300 import rl
+    spec = synth.motion(15, 0)
+    f32 = case(200, 64, spec)
+    with rl.Deconvolver(spec) as d:
+        u = d.run(f32, 20)  # numpy in, numpy out
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 20).u
+    assert oracle.rel_linf(u, ref) <= TOL
+
+
+def test_errors_are_reported():
+    from paper_1304_7211_gb300 import rl
+    ctx = rl.rl_create(0)
+    try:
+        f = torch.ones((8, 8), device="cuda")
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_iterate(ctx, f, None, f.clone(), 8, 8, 8, 3)
+        assert e.value.status == rl.RL_ERR_STATE
+        rl.rl_set_psf(ctx, synth.disc(8))  # extent 8 >= 8
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_iterate(ctx, f, None, f.clone(), 8, 8, 8, 3)
+        assert e.value.status == rl.RL_ERR_INVALID_ARG
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_iterate(ctx, f, None, f, 8, 8, 8, 3)  # u_out aliases f
+        assert e.value.status == rl.RL_ERR_INVALID_ARG
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_set_psf(ctx, synth.dense([[1.0, -1.0, 1.0]]))
+        assert e.value.status == rl.RL_ERR_INVALID_ARG
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_set_psf(ctx, synth.dense([[0.0, 0.0]]))
+        assert e.value.status == rl.RL_ERR_INVALID_ARG
+    finally:
+        rl.rl_destroy(ctx)
+    ctx = rl.rl_create(0, path="runsum")
+    try:
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_set_psf(ctx, synth.disc(3))
+        assert e.value.status == rl.RL_ERR_UNSUPPORTED
+    finally:
+        rl.rl_destroy(ctx)
+    ctx = rl.rl_create(0, path="span")
+    try:
+        with pytest.raises(rl.RLError) as e:
+            rl.rl_set_psf(ctx, synth.gaussian(5, 1.0))
+        assert e.value.status == rl.RL_ERR_UNSUPPORTED
+    finally:
+        rl.rl_destroy(ctx)
+
+
+# ---- invariants at the benchmark size ----------------------------------------
+
+@pytest.mark.parametrize("spec", synth.CONFIG2_PSFS, ids=lambda s: s.name)
+def test_full_size_launch_configuration(spec):
+    """2048 x 2048 in the benchmark's launch configuration: element-wise
+    parity with the oracle after 3 iterations, and flux / nonnegativity after
+    the full 200 iterations."""
+    c = synth.config2(spec)
+    f32 = c.f.astype(np.float32)
+    f64 = f32.astype(np.float64)
+    u3, _ = gpu_rl(spec, f32, 3)
+    ref3 = oracle.rl(f64, oracle_psf(spec), 3).u
+    assert oracle.rel_linf(u3, ref3) <= TOL
+    u, st = gpu_rl(spec, f32, c.iterations)
+    assert u.min() >= 0.0
+    assert abs(u.sum() - f64.sum()) <= 1e-4 * f64.sum()
+
+
+@pytest.mark.parametrize("spec", synth.CONFIG2_PSFS, ids=lambda s: s.name)
+def test_200_iterations_against_oracle(spec):
+    """The full iteration count of the 2048 x 2048 workload on a 512 x 512
+    image from the same generator: element-wise parity after 200 iterations."""
+    c = synth.config2(spec, size=512)
+    f32 = c.f.astype(np.float32)
+    u, _ = gpu_rl(spec, f32, c.iterations)
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), c.iterations).u
+    err = oracle.rel_linf(u, ref)
+    print(f"{spec.name}: 200 it rel_linf={err:.3e}")
+    assert err <= TOL
+
+
+def test_constant_image_is_reproduced():
+    f32 = np.full((300, 310), 77.0, np.float32)
+    for spec in (synth.motion(31, 0), synth.motion(31, 1), synth.disc(8), synth.gaussian(7, 1.5)):
+        for boundary in ("mirror", "clamp"):
+            u, _ = gpu_rl(spec, f32, 20, boundary=boundary)
+            np.testing.assert_allclose(u, 77.0, rtol=2e-6)
+
+
+# ---- storage modes --------------------------------------------------------------
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 3e-2), ("f16", 4e-3)])
+@pytest.mark.parametrize("spec", [synth.motion(15, 0), synth.motion(15, 1), synth.disc(4),
+                                  synth.gaussian(7, 1.5)], ids=lambda s: s.name)
+def test_reduced_precision_storage(spec, storage, tol):
+    """BF16/FP16 storage of f and u with FP32 arithmetic: the error against
+    the FP64 oracle (run on the same rounded f) is bounded by the format's
+    rounding, accumulated over the iterations."""
+    f32 = case(180, 140, spec)
+    dt = {"bf16": torch.bfloat16, "f16": torch.float16}[storage]
+    f_r = torch.from_numpy(f32).to(dt).float().numpy()
+    u, _ = gpu_rl(spec, f_r, 30, storage=storage)
+    ref = oracle.rl(f_r.astype(np.float64), oracle_psf(spec), 30).u
+    err = oracle.rel_linf(u, ref)
+    print(f"{storage} {spec.name}: rel_linf={err:.2e}")
+    assert err <= tol
+
+
+# ---- selective convolution (Eq. 4-5) -------------------------------------------
+
+def test_zero_threshold_equals_plain():
+    from paper_1304_7211_gb300 import rl
+    for spec in (synth.motion(15, 0), synth.motion(15, 1), synth.disc(4), synth.gaussian(7, 1.5)):
+        f32 = case(150, 120, spec)
+        plain, _ = gpu_rl(spec, f32, 25)
+        for q in (1, 10):
+            thin, st = gpu_rl(spec, f32, 25, thin=rl.thinning(0.0, update_period=q))
+            np.testing.assert_array_equal(thin, plain)
+            assert st.active_pixel_iterations == 150 * 120 * 25
+
+
+def test_infinite_threshold_keeps_only_full_iterations():
+    from paper_1304_7211_gb300 import rl
+    for spec in (synth.motion(15, 0), synth.motion(15, 1), synth.disc(4)):
+        f32 = case(140, 110, spec)
+        for K in (9, 10, 11, 23):
+            thin, st = gpu_rl(spec, f32, K, thin=rl.thinning(math.inf))
+            plain, _ = gpu_rl(spec, f32, -(-K // 10))
+            np.testing.assert_array_equal(thin, plain)
+            assert st.active_pixel_iterations == 140 * 110 * (-(-K // 10))
+
+
+@pytest.mark.parametrize("relative,tau,q", [(True, 1e-4, 1), (True, 1e-3, 1), (True, 1e-4, 10),
+                                            (False, 0.01, 1), (False, 0.05, 10)])
+@pytest.mark.parametrize("spec,path", [(synth.disc(4), "span"), (synth.disc(4), "stencil"),
+                                       (synth.motion(15, 0), "runsum"),
+                                       (synth.motion(15, 1), "runsum")],
+                         ids=lambda v: getattr(v, "name", v))
+def test_thinned_matches_oracle(spec, path, relative, tau, q):
+    """Images within max(1e-4, 10 tau') (tau' = tau relative to the image
+    scale) of the oracle; the final masks disagree on at most 2 % of pixels
+    and the active pixel-iteration counts within 2 %.  Disagreements come
+    only from pixels whose change lies within FP32 rounding of tau."""
+    from paper_1304_7211_gb300 import rl
+    K = 34
+    f32 = case(170, 150, spec, seed=synth.SEED_BASE + 52)
+    f64 = f32.astype(np.float64)
+    th = rl.thinning(tau, relative=relative, update_period=q)
+    u, st, mask = gpu_rl(spec, f32, K, path=path, thin=th, want_mask=True)
+    res = oracle.rl(f64, oracle_psf(spec), K, threshold=tau, relative=relative,
+                    update_period=q)
+    nxt = oracle.rl(f64, oracle_psf(spec), K + 1, threshold=tau, relative=relative,
+                    update_period=q, want_mask=True).mask_trace[K]
+    scale = tau if relative else tau / float(np.max(res.u))
+    err = oracle.rel_linf(u, res.u)
+    dis = int(np.sum(mask != nxt))
+    act_rel = abs(st.active_pixel_iterations - res.active_pixel_iterations) / res.active_pixel_iterations
+    print(f"{spec.name} {path} tau={tau} q={q}: err={err:.2e} mask_disagree={dis} act_rel={act_rel:.2e}")
+    assert err <= max(TOL, 10 * scale)
+    assert dis <= 0.02 * mask.size
+    assert act_rel <= 0.02
+    assert res.active_pixel_iterations < K * f32.size  # thinning did something
