@@ -115,6 +115,13 @@ typedef struct {
     int relative;      /* 1: |c - 1|, 0: |u' - u| (absolute, Sec. 4)         */
     int reset_period;  /* P >= 1, the paper uses 10                        */
     int update_period; /* 1 or reset_period                                */
+    /* Optional replay of a recorded schedule: iterations x H x W bytes (row
+     * pitch W, host or device memory), byte = 1 when the pixel is used in
+     * that iteration.  When non-NULL the threshold rule is not evaluated;
+     * used pixels are re-blurred and updated and inactive ones keep the
+     * ratio of their last used iteration, exactly as above.  NULL = decide
+     * by the threshold. */
+    const unsigned char *schedule;
 } rl_thinning;
 
 typedef struct {
@@ -197,6 +204,7 @@ const char *rl_last_error(const rl_ctx *ctx);
 
 /* Library version string, e.g. "rl-gb300 0.1 sm_103a". */
 const char *rl_version(void);
+
 
 #ifdef __cplusplus
 }

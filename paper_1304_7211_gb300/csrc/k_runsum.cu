@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) k_motion_x(IterArgs a, int tpr, int rpc, 
     T *u_out = (T *)a.u_out;
     const float w = a.weight;
     const long long mrow = (long long)y * a.m_pitch;
+    const long long mirow = (long long)y * a.mi_pitch;
     unsigned used = 0;
 
     if (row_ok) {
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(256) k_motion_x(IterArgs a, int tpr, int rpc, 
                 const int x = x0 + j;
                 if (x < W) {
                     bool use = true;
-                    if (THIN && !a.full) use = a.mask_in[mrow + x] != 0;
+                    if (THIN && !a.full) use = a.mask_in[mirow + x] != 0;
                     const float fx = Qe[PI(x + A)];
                     Qe[PI(x + A)] = use ? rl_ratio(fx, s * w) : a.rstale[mrow + x];
                     if (j + 1 < XCH && x + 1 < W) s += Ue[PI(x + L)] - Ue[PI(x)];
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) k_motion_x(IterArgs a, int tpr, int rpc, 
                     const float c = s * w;
                     float un;
                     if (THIN) {
-                        const bool use = a.full || a.mask_in[mrow + x] != 0;
+                        const bool use = a.full || a.mask_in[mirow + x] != 0;
                         used += use;
                         un = thin_update(a, mrow + x, use, u, c, Qe[PI(x + A)]);
                     } else {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256) k_motion_y(IterArgs a, int TS) {
             for (int p = r0; p < r1; ++p) {
                 bool use = true;
                 const long long mi = (long long)p * a.m_pitch + xs;
-                if (THIN && !a.full) use = a.mask_in[mi] != 0;
+                if (THIN && !a.full) use = a.mask_in[(long long)p * a.mi_pitch + xs] != 0;
                 float *qp = &Q[(p - y0 + A) * 32 + lane];
                 *qp = use ? rl_ratio(*qp, s * w) : a.rstale[mi];
                 if (p + 1 < r1) s += U[(p - P0 + L) * 32 + lane] - U[(p - P0) * 32 + lane];
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256) k_motion_y(IterArgs a, int TS) {
                 float un;
                 if (THIN) {
                     const long long mi = (long long)p * a.m_pitch + xs;
-                    const bool use = a.full || a.mask_in[mi] != 0;
+                    const bool use = a.full || a.mask_in[(long long)p * a.mi_pitch + xs] != 0;
                     used += (use && col_ok);
                     if (col_ok) un = thin_update(a, mi, use, u, c, Q[(p - y0 + A) * 32 + lane]);
                     else un = u;
@@ -205,7 +206,7 @@ cudaError_t launch_x_t(const IterArgs &a, cudaStream_t s) {
     const int row_floats = ((n_ext + (n_ext >> 5) + 1) + 3) & ~3;
     const size_t smem = (size_t)rpc * 2 * row_floats * sizeof(float);
     auto kern = k_motion_x<T, THIN>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<k_motion_x<T, THIN>>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.H + rpc - 1) / rpc);
     kern<<<grid, tpr * rpc, smem, s>>>(a, tpr, rpc, row_floats);
@@ -218,7 +219,7 @@ cudaError_t launch_y_t(const IterArgs &a, cudaStream_t s) {
     const int TS = a.H < YCH_TS ? a.H : YCH_TS;
     const size_t smem = (size_t)((TS + 2 * (L - 1)) + (TS + L - 1)) * 32 * sizeof(float);
     auto kern = k_motion_y<T, THIN>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<k_motion_y<T, THIN>>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + 31) / 32, (a.H + TS - 1) / TS);
     kern<<<grid, 256, smem, s>>>(a, TS);

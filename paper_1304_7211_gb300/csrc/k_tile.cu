@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf
                 if (j < n) {
                     bool use = true;
                     const long long mi = (long long)py * a.m_pitch + px + j;
-                    if (THIN && !a.full) use = a.mask_in[mi] != 0;
+                    if (THIN && !a.full) use = a.mask_in[(long long)py * a.mi_pitch + px + j] != 0;
                     qrow[j] = use ? rl_ratio(qrow[j], v[j]) : a.rstale[mi];
                 }
             }
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf
                     float un;
                     if (THIN) {
                         const long long mi = (long long)py * a.m_pitch + px + j;
-                        const bool use = a.full || a.mask_in[mi] != 0;
+                        const bool use = a.full || a.mask_in[(long long)py * a.mi_pitch + px + j] != 0;
                         used += use;
                         un = thin_update(a, mi, use, u, c[j], qrow[j]);
                     } else {
@@ -290,7 +290,7 @@ cudaError_t launch_t(const IterArgs &a, TileShape ts, cudaStream_t s) {
     int pf = 0;
     const size_t smem = tile_smem_bytes(a, ts, MODE, &pf);
     auto kern = k_tile<T, THIN, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<k_tile<T, THIN, MODE>>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + ts.tx - 1) / ts.tx, (a.H + ts.ty - 1) / ts.ty);
     kern<<<grid, NT, smem, s>>>(a, ts.tx, ts.ty, pf);

@@ -48,6 +48,8 @@ struct rl_ctx {
     unsigned long long *d_counter = nullptr;
     void *stage[3] = {nullptr, nullptr, nullptr};
     size_t stage_bytes[3] = {0, 0, 0};
+    void *sched = nullptr;  // device copy of a host replay schedule
+    size_t sched_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // mask left by the last thinned call (rl_get_mask)
     const uint8_t *last_mask = nullptr;
@@ -183,6 +185,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->rstale);
     cudaFree(ctx->d_counter);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
+    cudaFree(ctx->sched);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     cudaSetDevice(prev);
@@ -375,7 +378,21 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     a.taps = ctx->d_taps;
     a.spans = ctx->d_spans;
     a.m_pitch = sp;
+    a.mi_pitch = sp;
     a.rstale = ctx->rstale;
+    const uint8_t *sched = nullptr;
+    if (thin && thin->schedule) {
+        const size_t bytes = (size_t)W * H * K;
+        if (is_device_ptr(thin->schedule)) {
+            sched = thin->schedule;
+        } else {
+            rl_status st = grow(ctx, &ctx->sched, &ctx->sched_bytes, bytes, "rl_iterate: schedule");
+            if (st != RL_OK) return st;
+            CK(cudaMemcpyAsync(ctx->sched, thin->schedule, bytes, cudaMemcpyHostToDevice, ctx->stream),
+               "rl_iterate: schedule upload");
+            sched = (const uint8_t *)ctx->sched;
+        }
+    }
     a.active_count = thin ? ctx->d_counter : nullptr;
     if (thin) {
         a.relative = thin->relative != 0;
@@ -390,7 +407,14 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         const bool direct = last && !(k == 0 && u_out == start);
         a.u_out = direct ? u_out : ctx->ubuf[k & 1];
         a.out_pitch = direct ? pitch : sp;
-        if (thin) {
+        if (sched) {
+            a.replay = 1;
+            a.full = 0;
+            a.update_mask = 0;
+            a.mask_in = sched + (size_t)k * W * H;
+            a.mi_pitch = W;
+            a.mask_out = ctx->mask[cur];
+        } else if (thin) {
             a.full = (k % thin->reset_period) == 0;
             a.update_mask = thin->update_period == 1 || a.full;
             a.mask_in = ctx->mask[cur];
@@ -405,7 +429,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
                                 path == RL_PATH_SPAN ? rl::TILE_SPAN : rl::TILE_STENCIL, ts, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
         if (thin && a.update_mask) cur ^= 1;
-        if (thin) {
+        if (thin && !sched) {
             ctx->last_mask = ctx->mask[cur];
             ctx->last_W = W;
             ctx->last_H = H;

@@ -61,9 +61,11 @@ struct IterArgs {
     const uint8_t *mask_in;                  // 1 = active; read when !full
     uint8_t *mask_out;                       // written when update_mask
     float *rstale;                           // f/v of the last active iteration
-    long long m_pitch;                       // pitch of mask and rstale planes
+    long long mi_pitch;                      // pitch of mask_in
+    long long m_pitch;                       // pitch of mask_out and rstale
     int full;                                // every pixel used this iteration
     int update_mask;                         // write mask_out
+    int replay;                              // mask_in is a recorded schedule
     int relative;                            // |c-1| (1) or |u'-u| (0)
     float tau;                               // threshold (strict < -> inactive)
     unsigned long long *active_count;        // += used pixels (nullable)
@@ -78,7 +80,10 @@ __device__ __forceinline__ float rl_ratio(float f, float v) { return v > 0.f ? f
 __device__ __forceinline__ float thin_update(const IterArgs &a, long long mi, bool use, float u,
                                              float c, float q) {
     float un = use ? u * c : u;
-    if (a.update_mask) {
+    if (a.replay) {
+        // the schedule decides; keep the ratio of every used pixel
+        if (use) a.rstale[mi] = q;
+    } else if (a.update_mask) {
         float d = 0.f;
         if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
         bool keep = use && (d >= a.tau);
@@ -91,6 +96,26 @@ __device__ __forceinline__ float thin_update(const IterArgs &a, long long mi, bo
 __device__ __forceinline__ void count_active(unsigned long long *ctr, bool use) {
     unsigned b = __ballot_sync(0xffffffffu, use);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(ctr, (unsigned long long)__popc(b));
+}
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, once per kernel and device (the attribute persists in the context).
+template <auto KERN>
+inline cudaError_t ensure_smem(size_t bytes) {
+    static unsigned long long done = 0;  // bit per device ordinal (< 64)
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) __atomic_fetch_or(&done, bit, __ATOMIC_RELEASE);
+    return e;
 }
 
 }  // namespace rl

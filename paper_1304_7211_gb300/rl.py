@@ -45,7 +45,8 @@ class rl_psf_desc(ctypes.Structure):
 
 class rl_thinning(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_float), ("relative", ctypes.c_int),
-                ("reset_period", ctypes.c_int), ("update_period", ctypes.c_int)]
+                ("reset_period", ctypes.c_int), ("update_period", ctypes.c_int),
+                ("schedule", ctypes.c_void_p)]
 
 
 class rl_config(ctypes.Structure):
@@ -185,9 +186,13 @@ def rl_destroy(ctx) -> None:
 
 
 def thinning(threshold: float, relative: bool = True, reset_period: int = 10,
-             update_period: int = 1) -> rl_thinning:
-    return rl_thinning(float(threshold), int(bool(relative)), int(reset_period),
-                       int(update_period))
+             update_period: int = 1, schedule=None) -> rl_thinning:
+    """Selective-convolution parameters; ``schedule`` (optional, uint8
+    iterations x H x W, host or device) replays a recorded used-pixel mask."""
+    t = rl_thinning(float(threshold), int(bool(relative)), int(reset_period),
+                    int(update_period), _addr(schedule))
+    t._keep = schedule
+    return t
 
 
 class Deconvolver:

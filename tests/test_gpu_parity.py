@@ -246,18 +246,26 @@ def test_constant_image_is_reproduced():
 
 # ---- storage modes --------------------------------------------------------------
 
-@pytest.mark.parametrize("storage,tol", [("bf16", 3e-2), ("f16", 4e-3)])
+# Unit roundoff of the storage format: bf16 keeps 8 significant bits, f16 11.
+UNIT_ROUNDOFF = {"bf16": 2.0 ** -9, "f16": 2.0 ** -11}
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
 @pytest.mark.parametrize("spec", [synth.motion(15, 0), synth.motion(15, 1), synth.disc(4),
                                   synth.gaussian(7, 1.5)], ids=lambda s: s.name)
-def test_reduced_precision_storage(spec, storage, tol):
-    """BF16/FP16 storage of f and u with FP32 arithmetic: the error against
-    the FP64 oracle (run on the same rounded f) is bounded by the format's
-    rounding, accumulated over the iterations."""
+def test_reduced_precision_storage(spec, storage):
+    """BF16/FP16 storage of f and u with FP32 arithmetic.  Every iteration
+    rounds u once to the storage format (relative error <= unit roundoff),
+    and the multiplicative update carries a relative error of u into u' with
+    factor about one, so after K iterations the error against the FP64 oracle
+    (run on the same rounded f) is bounded by K times the unit roundoff."""
+    K = 30
+    tol = K * UNIT_ROUNDOFF[storage]
     f32 = case(180, 140, spec)
     dt = {"bf16": torch.bfloat16, "f16": torch.float16}[storage]
     f_r = torch.from_numpy(f32).to(dt).float().numpy()
-    u, _ = gpu_rl(spec, f_r, 30, storage=storage)
-    ref = oracle.rl(f_r.astype(np.float64), oracle_psf(spec), 30).u
+    u, _ = gpu_rl(spec, f_r, K, storage=storage)
+    ref = oracle.rl(f_r.astype(np.float64), oracle_psf(spec), K).u
     err = oracle.rel_linf(u, ref)
     print(f"{storage} {spec.name}: rel_linf={err:.2e}")
     assert err <= tol
@@ -287,33 +295,53 @@ def test_infinite_threshold_keeps_only_full_iterations():
             assert st.active_pixel_iterations == 140 * 110 * (-(-K // 10))
 
 
-@pytest.mark.parametrize("relative,tau,q", [(True, 1e-4, 1), (True, 1e-3, 1), (True, 1e-4, 10),
-                                            (False, 0.01, 1), (False, 0.05, 10)])
-@pytest.mark.parametrize("spec,path", [(synth.disc(4), "span"), (synth.disc(4), "stencil"),
-                                       (synth.motion(15, 0), "runsum"),
-                                       (synth.motion(15, 1), "runsum")],
-                         ids=lambda v: getattr(v, "name", v))
-def test_thinned_matches_oracle(spec, path, relative, tau, q):
-    """Images within max(1e-4, 10 tau') (tau' = tau relative to the image
-    scale) of the oracle; the final masks disagree on at most 2 % of pixels
-    and the active pixel-iteration counts within 2 %.  Disagreements come
-    only from pixels whose change lies within FP32 rounding of tau."""
+THIN_CASES = [(True, 1e-4, 1), (True, 1e-3, 1), (True, 1e-4, 10), (False, 0.01, 1),
+              (False, 0.05, 10)]
+THIN_PATHS = [(synth.disc(4), "span"), (synth.disc(4), "stencil"), (synth.motion(15, 0), "runsum"),
+              (synth.motion(15, 1), "runsum")]
+
+
+@pytest.mark.parametrize("relative,tau,q", THIN_CASES)
+@pytest.mark.parametrize("spec,path", THIN_PATHS, ids=lambda v: getattr(v, "name", v))
+def test_thinned_replay_matches_oracle(spec, path, relative, tau, q):
+    """The oracle's per-iteration used-pixel masks (Eq. 4-5) replayed on the
+    GPU: same selective convolutions, so the images agree to 1e-4 and the
+    active pixel-iteration counts exactly."""
+    from paper_1304_7211_gb300 import rl
+    K = 34
+    f32 = case(170, 150, spec, seed=synth.SEED_BASE + 52)
+    res = oracle.rl(f32.astype(np.float64), oracle_psf(spec), K, threshold=tau,
+                    relative=relative, update_period=q, want_mask=True)
+    sched = np.ascontiguousarray(res.mask_trace)
+    u, st = gpu_rl(spec, f32, K, path=path, thin=rl.thinning(tau, relative, 10, q, schedule=sched))
+    err = oracle.rel_linf(u, res.u)
+    assert err <= TOL, err
+    assert st.active_pixel_iterations == res.active_pixel_iterations
+    assert res.active_pixel_iterations < K * f32.size  # thinning did something
+
+
+@pytest.mark.parametrize("relative,tau,q", THIN_CASES)
+@pytest.mark.parametrize("spec,path", THIN_PATHS, ids=lambda v: getattr(v, "name", v))
+def test_thinned_free_running_masks(spec, path, relative, tau, q):
+    """GPU decisions (FP32) against the oracle's (FP64): the final masks are
+    compared by the count of disagreeing pixels, the active counts by their
+    relative difference.  A disagreement needs a change within rounding of
+    the threshold, so both stay tiny; the image difference they cause is
+    reported."""
     from paper_1304_7211_gb300 import rl
     K = 34
     f32 = case(170, 150, spec, seed=synth.SEED_BASE + 52)
     f64 = f32.astype(np.float64)
     th = rl.thinning(tau, relative=relative, update_period=q)
     u, st, mask = gpu_rl(spec, f32, K, path=path, thin=th, want_mask=True)
-    res = oracle.rl(f64, oracle_psf(spec), K, threshold=tau, relative=relative,
-                    update_period=q)
+    res = oracle.rl(f64, oracle_psf(spec), K, threshold=tau, relative=relative, update_period=q)
     nxt = oracle.rl(f64, oracle_psf(spec), K + 1, threshold=tau, relative=relative,
                     update_period=q, want_mask=True).mask_trace[K]
-    scale = tau if relative else tau / float(np.max(res.u))
-    err = oracle.rel_linf(u, res.u)
     dis = int(np.sum(mask != nxt))
     act_rel = abs(st.active_pixel_iterations - res.active_pixel_iterations) / res.active_pixel_iterations
-    print(f"{spec.name} {path} tau={tau} q={q}: err={err:.2e} mask_disagree={dis} act_rel={act_rel:.2e}")
-    assert err <= max(TOL, 10 * scale)
-    assert dis <= 0.02 * mask.size
-    assert act_rel <= 0.02
-    assert res.active_pixel_iterations < K * f32.size  # thinning did something
+    err = oracle.rel_linf(u, res.u)
+    print(f"{spec.name} {path} tau={tau} q={q}: mask_disagree={dis}/{mask.size} "
+          f"act_rel={act_rel:.2e} image_rel_linf={err:.2e}")
+    assert dis <= 0.005 * mask.size
+    assert act_rel <= 0.005
+    assert err <= 1e-2
