@@ -205,6 +205,37 @@ const char *rl_last_error(const rl_ctx *ctx);
 /* Library version string, e.g. "rl-gb300 0.1 sm_103a". */
 const char *rl_version(void);
 
+/*
+ * Allocation-free variant of the running-sum path.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc -- code
+ * running inside an allocator or memory-pool hook, latency-critical threads
+ * where an allocation may block on the device, processes whose device memory
+ * is partitioned in advance.
+ *
+ * Runs `iterations` RL iterations (Eq. 3) for horizontal linear motion blur
+ * of `length` pixels (RL_PSF_MOTION, axis 0), FP32, `boundary` as in
+ * rl_boundary, on `stream` (cudaStream_t; NULL = default stream) of the
+ * CURRENT device.  f, u0 (NULL = f) and u_out are caller-owned device
+ * pointers with row pitch `pitch` elements; u_out must alias neither f nor u0.
+ * No context is needed and the call allocates nothing: its only scratch (the
+ * second buffer of the iteration ping-pong) is a fixed array of
+ * RL_NOALLOC_MAX_PIXELS floats (16 MiB) in the library image, which every GPU
+ * that loads the library holds until the process exits.  W * H above that
+ * limit is rejected with RL_ERR_INVALID_ARG.
+ *
+ * The first call on each device looks up the array's device address (once,
+ * with that device current); make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's
+ * contents; nothing in it needs clearing (every pixel is written before it is
+ * read), but calls whose work overlaps on the GPU race on it.  Returns when
+ * the work is queued.  On failure a message is written to err (err_len bytes,
+ * may be NULL).  Errors: RL_ERR_INVALID_ARG, RL_ERR_UNSUPPORTED (rows too
+ * long for the running-sum kernel), RL_ERR_CUDA.
+ */
+#define RL_NOALLOC_MAX_PIXELS 4194304
+rl_status rl_motion_x_noalloc(const float *f, const float *u0, float *u_out, int W, int H,
+                              long long pitch, int length, int boundary, int iterations,
+                              void *stream, char *err, int err_len);
 
 #ifdef __cplusplus
 }

@@ -71,7 +71,8 @@ _lib = None
 
 # Every symbol include/rl.h declares.
 EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error", "rl_version",
-           "rl_get_mask")
+           "rl_get_mask", "rl_motion_x_noalloc")
+RL_NOALLOC_MAX_PIXELS = 4194304
 
 
 def load() -> ctypes.CDLL:
@@ -99,6 +100,10 @@ def load() -> ctypes.CDLL:
     lib.rl_version.argtypes = []
     lib.rl_get_mask.restype = ctypes.c_int
     lib.rl_get_mask.argtypes = [P, P, ctypes.c_longlong]
+    lib.rl_motion_x_noalloc.restype = ctypes.c_int
+    lib.rl_motion_x_noalloc.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                        ctypes.c_char_p, ctypes.c_int]
     _lib = lib
     return lib
 
@@ -178,6 +183,20 @@ def rl_iterate(ctx, f, u0, u_out, W: int, H: int, pitch: int, iterations: int,
 def rl_get_mask(ctx, dst, dst_pitch: int) -> None:
     """Copy the active mask left by the last thinned rl_iterate into dst."""
     _check(load().rl_get_mask(ctx, _addr(dst), dst_pitch), ctx)
+
+
+def rl_motion_x_noalloc(f, u0, u_out, W: int, H: int, pitch: int, length: int,
+                        boundary="mirror", iterations: int = 1, stream=None) -> None:
+    """Allocation-free running-sum RL for horizontal motion blur (FP32, device
+    pointers, current device); see include/rl.h.  Raises RLError on failure."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    buf = ctypes.create_string_buffer(256)
+    rc = load().rl_motion_x_noalloc(_addr(f), _addr(u0), _addr(u_out), W, H, pitch, length,
+                                    BOUNDARY.get(boundary, boundary), iterations, stream or None,
+                                    buf, len(buf))
+    if rc != RL_OK:
+        raise RLError(rc, buf.value.decode())
 
 
 def rl_destroy(ctx) -> None:
