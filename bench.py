@@ -162,6 +162,29 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def run_case(args):
+    """One solve of one PSF at --size for --iters iterations (for ncu)."""
+    import numpy as np
+    import torch
+    from paper_1304_7211_gb300 import _build, rl, synth
+    _build.build()
+    specs = {s.name: s for s in (synth.motion(31, 0), synth.motion(31, 1), synth.disc(8),
+                                 synth.disc(12), synth.gaussian(7, 1.5), synth.motion(15, 0))}
+    spec = specs[args.case]
+    g = synth.latent_image(args.size, args.size, synth.SEED_BASE + 2)
+    f32 = np.maximum(synth.blur(g, spec), 0.0).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    u = torch.empty_like(f)
+    with rl.Deconvolver(spec, path=args.path) as d:
+        rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters)
+        torch.cuda.synchronize()
+        st = rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters,
+                           stats=True)
+    print(f"case {spec.name} {args.size}^2 x {args.iters} it: {st.device_ms:.3f} ms "
+          f"({st.device_ms / args.iters * 1e3:.1f} us/it) path={rl.PATH_NAME[st.path]}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,10 +192,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="profiling mode: run one solve of this PSF (e.g. disc8, motionx31, "
+                         "motiony31, dense7x7) and print its time; no JSON line")
+    ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--path", default="auto")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.case:
+        return run_case(args)
 
     import numpy as np
     import torch
@@ -284,7 +315,8 @@ def main():
         peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s, TFLOP/s (adds)
         achieved = flops / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"k_tile<span> ({dom})",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"k_disc_half<float,0,8,fwd>+<..,adj> ({dom}, both launches of one iteration)",
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (adds)"}
     else:
         bytes_ = px * 12
@@ -294,6 +326,9 @@ def main():
                 "peak_source": pk_kind}
     roof["per_solve_ms"] = per
 
+    # kernel launches inside the timed region: one per iteration on the
+    # running-sum paths, two (forward + adjoint half) on the disc path
+    launches_per_step = sum(ITERS * (2 if s[0].kind == "disc" else 1) for s in solves)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -303,7 +338,7 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * plane,
                     "d2h_bytes_per_step": 3 * plane},
-            "gpu_launches": 3 * ITERS * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(inputs)

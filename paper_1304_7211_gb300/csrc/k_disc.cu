@@ -1,0 +1,20 @@
+// k_disc.cu -- radius dispatch of the disc kernels.
+#include "rl_launch.h"
+
+namespace rl {
+
+cudaError_t launch_disc(const IterArgs &a, int storage, bool thin, int radius, float *qplane,
+                        long long q_pitch, cudaStream_t s) {
+    switch (radius) {
+#define RL_DISC_CASE(R) \
+    case R: return launch_disc_r##R(a, storage, thin, qplane, q_pitch, s);
+    RL_DISC_CASE(1) RL_DISC_CASE(2) RL_DISC_CASE(3) RL_DISC_CASE(4) RL_DISC_CASE(5)
+    RL_DISC_CASE(6) RL_DISC_CASE(7) RL_DISC_CASE(8) RL_DISC_CASE(9) RL_DISC_CASE(10)
+    RL_DISC_CASE(11) RL_DISC_CASE(12) RL_DISC_CASE(13) RL_DISC_CASE(14) RL_DISC_CASE(15)
+    RL_DISC_CASE(16)
+#undef RL_DISC_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rl

@@ -1,0 +1,222 @@
+// k_disc.cuh -- register-blocked generic box filter for the defocus disc
+// (Sec. 3 "Defocus blur"), one fused RL iteration (Eq. 3) per launch.
+//
+// The disc of radius R (pixel-centre inclusion) is a stack of horizontal runs:
+// PSF row ty covers tx in [-s(ty), s(ty)], s(ty) = floor(sqrt(R^2 - ty^2)).
+// Each thread owns a block of SY x SX outputs.  For every input row the block
+// touches, it loads the row segment [x0 - R, x0 + SX + R) once from shared
+// memory, forms its running (prefix) sum in registers -- short, so FP32
+// stays accurate -- and adds to each output row that uses this input row the
+// run sum P[j + R + 1 + s] - P[j + R - s]: sliding the PSF only exchanges the
+// run ends (Sec. 3), and with a prefix a run of any length costs one
+// difference.  R is a template parameter, so every run end is a compile-time
+// register index; the disc is symmetric, so the forward convolution and the
+// adjoint (h* = h reflected) use the same table.
+//
+// The iteration runs as two launches (forward + ratio into a q plane, then
+// adjoint + update): the disc path is bound by arithmetic, not HBM, so the
+// second 12 B/px of traffic is cheaper than recomputing the forward
+// convolution over a 2R apron, and each launch stages a single halo'd array
+// (more resident CTAs).  The q plane doubles as the stale ratio of Eq. 5:
+// inactive pixels are simply not rewritten.
+#pragma once
+
+#include "rl_launch.h"
+
+namespace rl {
+namespace disc {
+
+constexpr int SX = 8;  // outputs per thread along x
+constexpr int SY = 4;  // outputs per thread along y
+
+// Shared-memory column with one skew word every SX columns: a warp's 4 x 8
+// patch of blocks then reads 32 distinct banks (odd row pitch).
+__device__ __forceinline__ int sk(int c) { return c + (c >> 3); }
+
+// Half-width of the disc's run in PSF row ty: largest s with s^2 + ty^2 <= R^2.
+__host__ __device__ constexpr int run_half_width(int R, int ty) {
+    int t2 = ty * ty, s = 0;
+    while ((s + 1) * (s + 1) + t2 <= R * R) ++s;
+    return s;
+}
+
+__device__ __forceinline__ void warp_count_add(unsigned long long *ctr, unsigned cnt) {
+    unsigned s = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+
+// Stage rows [0, nrows) x columns [0, ncols) of an array with skewed columns:
+// element (r, c) is image pixel (y0 + r, x0 + c) when r in [r_lo, r_hi) and
+// c in [c_lo, c_hi) (boundary-mapped unless `inside`), else 0.  One warp per
+// row, four rows in flight.
+template <typename T>
+__device__ __forceinline__ void stage_rows(float *dst, int pitch, int nrows, int ncols, int r_hi,
+                                           int c_lo, int c_hi, bool inside, int clamp, int W,
+                                           int H, int y0, int x0, const T *src, long long sp,
+                                           int wid, int nwarps, int lane, int r_lo = 0) {
+    constexpr int RB = 4;
+    for (int rb = wid * RB; rb < nrows; rb += nwarps * RB) {
+        for (int cb = lane; cb < ncols; cb += 32) {
+            float v[RB];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const int r = rb + k;
+                v[k] = 0.f;
+                if (r < nrows && r >= r_lo && r < r_hi && cb >= c_lo && cb < c_hi) {
+                    int yy = y0 + r, xx = x0 + cb;
+                    if (!inside) {
+                        yy = bmap(yy, H, clamp);
+                        xx = bmap(xx, W, clamp);
+                    }
+                    v[k] = Stor<T>::ld(src, (long long)yy * sp + xx);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                if (rb + k < nrows) dst[(rb + k) * pitch + sk(cb)] = v[k];
+        }
+    }
+}
+
+// Sum of the disc over the block's SY x SX outputs.  Input row m of the
+// block is array row row0 + m; output row i uses it with ty = i + R - m
+// (forward) -- the adjoint reads the mirrored offset, which has the same run.
+template <int R>
+__device__ __forceinline__ void disc_block(const float *src, int pitch, int row0, int colblk,
+                                           float (&acc)[SY][SX]) {
+    constexpr int NW = SX + 2 * R;
+#pragma unroll
+    for (int i = 0; i < SY; ++i)
+#pragma unroll
+        for (int j = 0; j < SX; ++j) acc[i][j] = 0.f;
+    const float *base = src + row0 * pitch + colblk * (SX + 1);
+#pragma unroll
+    for (int m = 0; m < SY + 2 * R; ++m) {
+        const float *rp = base + m * pitch;
+        float P[NW + 1];
+        P[0] = 0.f;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) P[k + 1] = P[k] + rp[k + (k >> 3)];
+#pragma unroll
+        for (int i = 0; i < SY; ++i) {
+            const int ty = i + R - m;
+            if (ty < -R || ty > R) continue;
+            const int s = run_half_width(R, ty);
+#pragma unroll
+            for (int j = 0; j < SX; ++j) acc[i][j] += P[j + R + 1 + s] - P[j + R - s];
+        }
+    }
+}
+
+// One half of an RL iteration for a TILE x TILE output tile (128 threads, one
+// SY x SX block each).  FWD: v = h (x) u and q = f / v on the tile, written
+// to the q plane (inactive pixels keep their q: it is the ratio of their last
+// active iteration, Eq. 5).  !FWD: c = h* (x) q and u' = u c with the
+// selective-convolution bookkeeping.  The input plane (u or q) is staged with
+// a 2R halo continued across the image border.
+constexpr int TILE = 64;
+
+template <typename T, bool THIN, int R, bool FWD>
+__global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane, long long q_pitch) {
+    extern __shared__ float sm[];
+    constexpr int NS = TILE + 2 * R;           // staged rows and columns
+    constexpr int SP = (NS + (NS >> 3)) | 1;   // skewed, odd pitch
+    const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned used = 0;
+    {
+        const bool inside = x0 - R >= 0 && x0 + TILE + R <= a.W && y0 - R >= 0 && y0 + TILE + R <= a.H;
+        if (FWD)
+            stage_rows<T>(sm, SP, NS, NS, NS, 0, NS, inside, a.clamp, a.W, a.H, y0 - R, x0 - R,
+                          (const T *)a.u_in, a.in_pitch, wid, 4, lane);
+        else
+            stage_rows<float>(sm, SP, NS, NS, NS, 0, NS, inside, a.clamp, a.W, a.H, y0 - R, x0 - R,
+                              qplane, q_pitch, wid, 4, lane);
+    }
+    __syncthreads();
+    // warp w covers the 32 x 32 quarter (w & 1, w >> 1); lane = 4 (x) x 8 (y) blocks
+    const int bx = (wid & 1) * 4 + (lane & 3), by = (wid >> 1) * 8 + (lane >> 2);
+    float acc[SY][SX];
+    disc_block<R>(sm, SP, by * SY, bx, acc);
+    const int xb = x0 + bx * SX, yb = y0 + by * SY;
+#pragma unroll
+    for (int i = 0; i < SY; ++i) {
+        const int y = yb + i;
+        if (y >= a.H) break;
+#pragma unroll
+        for (int j = 0; j < SX; ++j) {
+            const int x = xb + j;
+            if (x >= a.W) break;
+            if (FWD) {
+                bool use = true;
+                if (THIN && !a.full) use = a.mask_in[(long long)y * a.mi_pitch + x] != 0;
+                if (use) {
+                    const float fv = Stor<T>::ld((const T *)a.f, (long long)y * a.f_pitch + x);
+                    qplane[(long long)y * q_pitch + x] = rl_ratio(fv, acc[i][j] * a.weight);
+                }
+            } else {
+                const float u = Stor<T>::ld((const T *)a.u_in, (long long)y * a.in_pitch + x);
+                const float c = acc[i][j] * a.weight;
+                float un = u * c;
+                if (THIN) {
+                    const bool use = a.full || a.mask_in[(long long)y * a.mi_pitch + x] != 0;
+                    used += use;
+                    un = use ? un : u;
+                    if (a.update_mask && !a.replay) {
+                        float d = 0.f;
+                        if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
+                        a.mask_out[(long long)y * a.m_pitch + x] = (uint8_t)(use && d >= a.tau);
+                    }
+                }
+                Stor<T>::st((T *)a.u_out, (long long)y * a.out_pitch + x, un);
+            }
+        }
+    }
+    if (!FWD && THIN && a.active_count) warp_count_add(a.active_count, used);
+}
+
+template <int R>
+constexpr size_t half_smem_bytes() {
+    constexpr int NS = TILE + 2 * R;
+    constexpr int SP = (NS + (NS >> 3)) | 1;
+    return (size_t)NS * SP * sizeof(float);
+}
+
+template <int R, typename T, bool THIN>
+cudaError_t launch_one(const IterArgs &a, float *qplane, long long q_pitch, cudaStream_t s) {
+    constexpr size_t smem = half_smem_bytes<R>();
+    cudaError_t e = ensure_smem<k_disc_half<T, THIN, R, true>>(smem);
+    if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, R, false>>(smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + TILE - 1) / TILE, (a.H + TILE - 1) / TILE);
+    k_disc_half<T, THIN, R, true><<<grid, 128, smem, s>>>(a, qplane, q_pitch);
+    k_disc_half<T, THIN, R, false><<<grid, 128, smem, s>>>(a, qplane, q_pitch);
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_r(const IterArgs &a, int storage, bool thin, float *qplane, long long q_pitch,
+                     cudaStream_t s) {
+    switch (storage) {
+    case ST_F32: return thin ? launch_one<R, float, true>(a, qplane, q_pitch, s)
+                             : launch_one<R, float, false>(a, qplane, q_pitch, s);
+    case ST_BF16: return thin ? launch_one<R, __nv_bfloat16, true>(a, qplane, q_pitch, s)
+                              : launch_one<R, __nv_bfloat16, false>(a, qplane, q_pitch, s);
+    case ST_F16: return thin ? launch_one<R, __half, true>(a, qplane, q_pitch, s)
+                             : launch_one<R, __half, false>(a, qplane, q_pitch, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace disc
+}  // namespace rl
+
+// One translation unit per radius keeps each compile short and lets them run
+// in parallel.
+#define RL_DISC_RADIUS_TU(R)                                                                 \
+    namespace rl {                                                                           \
+    cudaError_t launch_disc_r##R(const IterArgs &a, int storage, bool thin, float *qplane,   \
+                                 long long q_pitch, cudaStream_t s) {                        \
+        return disc::launch_r<R>(a, storage, thin, qplane, q_pitch, s);                      \
+    }                                                                                        \
+    }

@@ -1,0 +1,3 @@
+// Disc kernel instantiation for radius 6 (see k_disc.cuh).
+#include "k_disc.cuh"
+RL_DISC_RADIUS_TU(6)

@@ -50,11 +50,14 @@ __global__ void __launch_bounds__(256) k_motion_x(IterArgs a, int tpr, int rpc, 
     unsigned used = 0;
 
     if (row_ok) {
-        const long long urow = (long long)y * a.in_pitch;
-        for (int i = t; i < W + L - 1; i += tpr)
-            Ue[PI(i)] = Stor<T>::ld(u_in, urow + bmap(i - B, W, a.clamp));
-        const long long frow = (long long)y * a.f_pitch;
-        for (int x = t; x < W; x += tpr) Qe[PI(x + A)] = Stor<T>::ld(f, frow + x);
+        // interior of u and f with batched (vector) loads; the continued
+        // ends of u (A + B samples) with mapped scalar loads
+        const T *urow = u_in + (long long)y * a.in_pitch;
+        row_to_smem<4>(Ue, [B](int i) { return PI(i + B); }, urow, W, t, tpr);
+        row_to_smem<4>(Qe, [A](int i) { return PI(i + A); }, f + (long long)y * a.f_pitch, W, t, tpr);
+        gather_batched<4>(A + B, t, tpr,
+            [&](int i) { return Stor<T>::ld(urow, bmap(i < B ? i - B : W + i - B, W, a.clamp)); },
+            [&](int i, float v) { Ue[PI(i < B ? i : W + i)] = v; });
     }
     __syncthreads();
     // forward: v(x) = w * sum_{e=x-B}^{x+A} u(m(e)) = w * sum_k Ue[x + k]
@@ -107,10 +110,8 @@ __global__ void __launch_bounds__(256) k_motion_x(IterArgs a, int tpr, int rpc, 
         }
     }
     __syncthreads();
-    if (row_ok) {
-        const long long orow = (long long)y * a.out_pitch;
-        for (int x = t; x < W; x += tpr) Stor<T>::st(u_out, orow + x, Ue[PI(x + B)]);
-    }
+    if (row_ok)
+        smem_to_row(u_out + (long long)y * a.out_pitch, Ue, [B](int i) { return PI(i + B); }, W, t, tpr);
     if (THIN && a.active_count) warp_count_add(a.active_count, used);
 }
 
@@ -140,10 +141,13 @@ __global__ void __launch_bounds__(256) k_motion_y(IterArgs a, int TS) {
     const float w = a.weight;
     unsigned used = 0;
 
-    for (int r = wid; r < UL; r += NW)
-        U[r * 32 + lane] = Stor<T>::ld(u_in, (long long)bmap(P0 - B + r, H, a.clamp) * a.in_pitch + xs);
-    for (int p = P0 + wid; p < P1; p += NW)
-        Q[(p - y0 + A) * 32 + lane] = Stor<T>::ld(f, (long long)p * a.f_pitch + xs);
+    // each warp stages whole rows (lane = column), 8 rows in flight per thread
+    gather_batched<8>(UL, wid, NW,
+        [&](int r) { return Stor<T>::ld(u_in, (long long)bmap(P0 - B + r, H, a.clamp) * a.in_pitch + xs); },
+        [&](int r, float v) { U[r * 32 + lane] = v; });
+    gather_batched<8>(P1 - P0, wid, NW,
+        [&](int r) { return Stor<T>::ld(f, (long long)(P0 + r) * a.f_pitch + xs); },
+        [&](int r, float v) { Q[(P0 + r - y0 + A) * 32 + lane] = v; });
     __syncthreads();
     {  // forward over rows P: v(p) = w * sum_{e=p-B}^{p+A} u(m(e))
         const int n = P1 - P0, per = (n + NW - 1) / NW;

@@ -180,19 +180,28 @@ __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf
     } else {
         for (int i = threadIdx.x; i < kh * kw; i += NT) psf[i] = a.taps[i];
     }
-    // u over the extended region, continued at the borders
-    for (int i = threadIdx.x; i < g.UH * g.UW; i += NT) {
-        const int r = i / g.UW, c = i - r * g.UW;
-        const int yy = bmap(g.uy0 + r, a.H, a.clamp), xx = bmap(g.ux0 + c, a.W, a.clamp);
-        U[r * g.UP + c] = Stor<T>::ld(u_in, (long long)yy * a.in_pitch + xx);
-    }
-    // f on P, staged where q will be written
+    // u over the extended region, continued at the borders, and f on P
+    // (staged where q will be written); 8 loads in flight per thread
+    gather_batched<8>(g.UH * g.UW, threadIdx.x, NT,
+        [&](int i) {
+            const int r = i / g.UW, c = i - r * g.UW;
+            const int yy = bmap(g.uy0 + r, a.H, a.clamp), xx = bmap(g.ux0 + c, a.W, a.clamp);
+            return Stor<T>::ld(u_in, (long long)yy * a.in_pitch + xx);
+        },
+        [&](int i, float v) {
+            const int r = i / g.UW, c = i - r * g.UW;
+            U[r * g.UP + c] = v;
+        });
     const int PW = g.px1 - g.px0, PH = g.py1 - g.py0;
-    for (int i = threadIdx.x; i < PH * PW; i += NT) {
-        const int r = i / PW, c = i - r * PW;
-        Q[(g.py0 + r - g.qy0) * g.QP + (g.px0 + c - g.qx0)] =
-            Stor<T>::ld(f, (long long)(g.py0 + r) * a.f_pitch + g.px0 + c);
-    }
+    gather_batched<8>(PH * PW, threadIdx.x, NT,
+        [&](int i) {
+            const int r = i / PW, c = i - r * PW;
+            return Stor<T>::ld(f, (long long)(g.py0 + r) * a.f_pitch + g.px0 + c);
+        },
+        [&](int i, float v) {
+            const int r = i / PW, c = i - r * PW;
+            Q[(g.py0 + r - g.qy0) * g.QP + (g.px0 + c - g.qx0)] = v;
+        });
     __syncthreads();
 
     // q = f / (h (x) u) on P.  Item = (row, chunk); consecutive lanes take
@@ -262,11 +271,13 @@ __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf
     }
     __syncthreads();
     {
+        // one warp per output row, 16-byte stores where the row allows
         const int TWd = g.x1 - g.x0, THd = g.y1 - g.y0;
-        for (int i = threadIdx.x; i < THd * TWd; i += NT) {
-            const int r = i / TWd, c = i - r * TWd;
-            Stor<T>::st(u_out, (long long)(g.y0 + r) * a.out_pitch + g.x0 + c,
-                        U[(g.y0 + r - g.uy0) * g.UP + (g.x0 + c - g.ux0)]);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int r = wid; r < THd; r += NT / 32) {
+            const float *src = U + (g.y0 + r - g.uy0) * g.UP + (g.x0 - g.ux0);
+            smem_to_row(u_out + (long long)(g.y0 + r) * a.out_pitch + g.x0, src,
+                        [](int i) { return i; }, TWd, lane, 32);
         }
     }
     if (THIN && a.active_count) warp_count_add(a.active_count, used);

@@ -30,7 +30,7 @@ struct rl_ctx {
 
     // PSF plan
     bool has_psf = false;
-    int kind = 0, axis = 0;
+    int kind = 0, axis = 0, disc_radius = 0;
     int kw = 0, kh = 0, ax = 0, ay = 0;  // dense layout; bx = kw-1-ax, by = kh-1-ay
     std::vector<float> taps;             // normalised, row-major kh x kw
     bool uniform = false;                // one contiguous run of equal taps per row
@@ -45,6 +45,8 @@ struct rl_ctx {
     uint8_t *mask[2] = {nullptr, nullptr};
     float *rstale = nullptr;
     size_t thin_px = 0;
+    float *qplane = nullptr;  // ratio plane of the two-launch disc path
+    size_t q_px = 0;
     unsigned long long *d_counter = nullptr;
     void *stage[3] = {nullptr, nullptr, nullptr};
     size_t stage_bytes[3] = {0, 0, 0};
@@ -183,6 +185,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->mask[0]);
     cudaFree(ctx->mask[1]);
     cudaFree(ctx->rstale);
+    cudaFree(ctx->qplane);
     cudaFree(ctx->d_counter);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
     cudaFree(ctx->sched);
@@ -290,6 +293,7 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
 
     ctx->kind = d->kind;
     ctx->axis = d->kind == RL_PSF_MOTION ? d->axis : 0;
+    ctx->disc_radius = d->kind == RL_PSF_DISC ? d->radius : 0;
     ctx->kw = kw;
     ctx->kh = kh;
     ctx->ax = ax;
@@ -361,6 +365,20 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         }
         CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream),
            "rl_iterate: counter");
+        // the stale ratio of a pixel that was never used is 0
+        CK(cudaMemsetAsync(ctx->rstale, 0, plane * sizeof(float), ctx->stream), "rl_iterate: stale ratio");
+    }
+    const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
+                           ctx->disc_radius <= rl::kDiscMaxRadius;
+    if (disc_fast) {
+        if (ctx->q_px < plane) {
+            cudaFree(ctx->qplane);
+            ctx->qplane = nullptr;
+            ctx->q_px = 0;
+            CK(cudaMalloc(&ctx->qplane, plane * sizeof(float)), "rl_iterate: ratio plane");
+            ctx->q_px = plane;
+        }
+        if (thin) CK(cudaMemsetAsync(ctx->qplane, 0, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
     }
 
     IterArgs a;
@@ -424,6 +442,9 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         if (path == RL_PATH_RUNSUM)
             e = ctx->axis == 0 ? rl::launch_motion_x(a, ctx->storage, thin != nullptr, ctx->stream)
                                : rl::launch_motion_y(a, ctx->storage, thin != nullptr, ctx->stream);
+        else if (disc_fast)
+            e = rl::launch_disc(a, ctx->storage, thin != nullptr, ctx->disc_radius, ctx->qplane, sp,
+                                ctx->stream);
         else
             e = rl::launch_tile(a, ctx->storage, thin != nullptr,
                                 path == RL_PATH_SPAN ? rl::TILE_SPAN : rl::TILE_STENCIL, ts, ctx->stream);

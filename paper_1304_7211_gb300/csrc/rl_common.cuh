@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace rl {
 
@@ -29,6 +30,133 @@ template <> struct Stor<__half> {
     static __device__ __forceinline__ float ldc(const __half *p, long long i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half *p, long long i, float v) { p[i] = __float2half_rn(v); }
 };
+
+// 16-byte vectors of a storage type: VEC elements per 16-byte load/store.
+template <typename T> struct Vec16 { static constexpr int N = 16 / sizeof(T); };
+
+template <typename T>
+__device__ __forceinline__ void ld16(const T *p, float *out) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p));
+    if constexpr (sizeof(T) == 4) {
+        out[0] = __uint_as_float(r.x); out[1] = __uint_as_float(r.y);
+        out[2] = __uint_as_float(r.z); out[3] = __uint_as_float(r.w);
+    } else {
+        const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T lo, hi;
+            unsigned short a = (unsigned short)(w[k] & 0xffffu), b = (unsigned short)(w[k] >> 16);
+            memcpy(&lo, &a, 2);
+            memcpy(&hi, &b, 2);
+            out[2 * k] = Stor<T>::ldc(&lo, 0);
+            out[2 * k + 1] = Stor<T>::ldc(&hi, 0);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st16(T *p, const float *in) {
+    uint4 r;
+    if constexpr (sizeof(T) == 4) {
+        r.x = __float_as_uint(in[0]); r.y = __float_as_uint(in[1]);
+        r.z = __float_as_uint(in[2]); r.w = __float_as_uint(in[3]);
+    } else {
+        unsigned w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T lo, hi;
+            Stor<T>::st(&lo, 0, in[2 * k]);
+            Stor<T>::st(&hi, 0, in[2 * k + 1]);
+            unsigned short a, b;
+            memcpy(&a, &lo, 2);
+            memcpy(&b, &hi, 2);
+            w[k] = (unsigned)a | ((unsigned)b << 16);
+        }
+        r = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    *reinterpret_cast<uint4 *>(p) = r;
+}
+
+// Copy a contiguous run src[0, n) of a global row into shared memory,
+// element i going to dst[didx(i)].  Each of the nt cooperating threads (index
+// t) keeps BATCH independent loads in flight before it stores any; 16-byte
+// vector loads are used when the run starts on a 16-byte boundary.
+template <int BATCH, typename T, typename DI>
+__device__ __forceinline__ void row_to_smem(float *dst, DI didx, const T *src, int n, int t, int nt) {
+    constexpr int V = Vec16<T>::N;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int nv = n / V;
+        for (int base = t; base < nv; base += BATCH * nt) {
+            float v[BATCH][V];
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                const int i = base + j * nt;
+                if (i < nv) ld16(src + (long long)i * V, v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                const int i = base + j * nt;
+                if (i < nv) {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) dst[didx(i * V + k)] = v[j][k];
+                }
+            }
+        }
+        done = nv * V;
+    }
+    for (int base = done + t; base < n; base += BATCH * nt) {
+        float v[BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int i = base + j * nt;
+            if (i < n) v[j] = Stor<T>::ld(src, i);
+        }
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int i = base + j * nt;
+            if (i < n) dst[didx(i)] = v[j];
+        }
+    }
+}
+
+// Store a shared-memory run src[sidx(i)], i in [0, n), to a contiguous global
+// row dst[0, n), with 16-byte vector stores when dst is 16-byte aligned.
+template <typename T, typename SI>
+__device__ __forceinline__ void smem_to_row(T *dst, const float *src, SI sidx, int n, int t, int nt) {
+    constexpr int V = Vec16<T>::N;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        const int nv = n / V;
+        for (int i = t; i < nv; i += nt) {
+            float v[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[k] = src[sidx(i * V + k)];
+            st16(dst + (long long)i * V, v);
+        }
+        done = nv * V;
+    }
+    for (int i = done + t; i < n; i += nt) Stor<T>::st(dst, i, src[sidx(i)]);
+}
+
+// Gather n elements into shared memory through arbitrary index maps
+// (ld(i) -> float, st(i, v)), BATCH loads in flight per thread.
+template <int BATCH, typename LD, typename ST>
+__device__ __forceinline__ void gather_batched(int n, int t, int nt, LD ld, ST st) {
+    for (int base = t; base < n; base += BATCH * nt) {
+        float v[BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int i = base + j * nt;
+            if (i < n) v[j] = ld(i);
+        }
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int i = base + j * nt;
+            if (i < n) st(i, v[j]);
+        }
+    }
+}
 
 // ---- boundary continuation (Sec. 2) ----------------------------------------
 // clamp = closest image pixel; mirror = half-sample symmetric, 2n-periodic.

@@ -28,4 +28,19 @@ TileShape tile_shape_for(int ax, int bx, int ay, int by);
 cudaError_t launch_tile(const IterArgs &a, int storage, bool thin, int mode, TileShape ts,
                         cudaStream_t s);
 
+// Register-blocked disc kernels (k_disc.cuh, one translation unit per
+// radius): the defocus disc of radius 1..16 with compile-time runs.  One RL
+// iteration = two launches sharing the library-owned FP32 q plane.
+constexpr int kDiscMaxRadius = 16;
+cudaError_t launch_disc(const IterArgs &a, int storage, bool thin, int radius, float *qplane,
+                        long long q_pitch, cudaStream_t s);
+#define RL_DECLARE_DISC_R(R)                                                                 \
+    cudaError_t launch_disc_r##R(const IterArgs &a, int storage, bool thin, float *qplane,   \
+                                 long long q_pitch, cudaStream_t s);
+RL_DECLARE_DISC_R(1) RL_DECLARE_DISC_R(2) RL_DECLARE_DISC_R(3) RL_DECLARE_DISC_R(4)
+RL_DECLARE_DISC_R(5) RL_DECLARE_DISC_R(6) RL_DECLARE_DISC_R(7) RL_DECLARE_DISC_R(8)
+RL_DECLARE_DISC_R(9) RL_DECLARE_DISC_R(10) RL_DECLARE_DISC_R(11) RL_DECLARE_DISC_R(12)
+RL_DECLARE_DISC_R(13) RL_DECLARE_DISC_R(14) RL_DECLARE_DISC_R(15) RL_DECLARE_DISC_R(16)
+#undef RL_DECLARE_DISC_R
+
 }  // namespace rl
