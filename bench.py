@@ -326,9 +326,11 @@ def main():
                 "peak_source": pk_kind}
     roof["per_solve_ms"] = per
 
-    # kernel launches inside the timed region: one per iteration on the
-    # running-sum paths, two (forward + adjoint half) on the disc path
-    launches_per_step = sum(ITERS * (2 if s[0].kind == "disc" else 1) for s in solves)
+    # kernel launches inside the timed region, as counted by the library
+    launches_per_step = 0
+    for spec, d, f, u, _, _ in solves:
+        st = rl.rl_iterate(d.ctx, f, None, u, SIZE, SIZE, SIZE, ITERS, stats=True)
+        launches_per_step += st.launches
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

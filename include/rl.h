@@ -124,12 +124,18 @@ typedef struct {
     const unsigned char *schedule;
 } rl_thinning;
 
+/* rl_config.flags */
+#define RL_FLAG_PER_ITERATION 1 /* one launch per iteration even where the
+                                   running-sum path could keep whole rows
+                                   resident for all iterations            */
+
 typedef struct {
     int device;     /* CUDA device ordinal                                   */
     void *stream;   /* cudaStream_t to issue work on; NULL = default stream */
     int storage;    /* rl_storage of f, u0, u_out (and internal u buffers)  */
     int boundary;   /* rl_boundary                                          */
     int path;       /* rl_path                                              */
+    int flags;      /* RL_FLAG_* bits, 0 = defaults                         */
 } rl_config;
 
 typedef struct {
@@ -138,6 +144,7 @@ typedef struct {
     long long active_pixel_iterations;/* pixel-iterations actually re-blurred  */
     double device_ms;                 /* stream time of the call (CUDA events) */
     int path;                         /* rl_path that ran                      */
+    int launches;                     /* kernel launches the call issued       */
 } rl_stats;
 
 /*

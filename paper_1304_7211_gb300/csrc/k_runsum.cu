@@ -199,6 +199,136 @@ __global__ void __launch_bounds__(256) k_motion_y(IterArgs a, int TS) {
     if (THIN && a.active_count) warp_count_add(a.active_count, used);
 }
 
+// ---- motion along x, all iterations with the rows resident -------------------
+// Rows are independent under a motion PSF along x for every iteration, so a
+// CTA keeps its rows of u, q and f (and the selective-convolution mask) in
+// shared memory for all K iterations: HBM sees f and u0 read once and u_K
+// written once.  The arithmetic of each iteration is exactly that of
+// k_motion_x.  A value written at an interior position is also written to
+// the continued positions that map onto it, so each iteration needs two
+// barriers.  Inactive pixels keep their q entry: it is the ratio of their
+// last active iteration (Eq. 5).
+__device__ __forceinline__ void put_continued(float *E, int off, int x, float v, int W, int lo,
+                                              int hi, int clamp) {
+    // E holds extended coordinates [-lo, W + hi) at index e + lo; write v at
+    // x and at every continued position whose boundary map is x.
+    E[PI(x + off)] = v;
+    if (clamp) {
+        if (x == 0)
+            for (int i = 0; i < lo; ++i) E[PI(i)] = v;
+        if (x == W - 1)
+            for (int i = 0; i < hi; ++i) E[PI(W + lo + i)] = v;
+    } else {
+        if (x < lo) E[PI(lo - 1 - x)] = v;
+        if (x >= W - hi) E[PI(2 * W - 1 - x + lo)] = v;
+    }
+}
+
+template <typename T, bool THIN>
+__global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int tpr, int rpc,
+                                                     int line_floats, int mask_bytes) {
+    extern __shared__ float sm[];
+    const int W = a.W, A = a.ax, B = a.bx, L = A + B + 1;
+    const int g = threadIdx.x / tpr, t = threadIdx.x - g * tpr;
+    const int y = blockIdx.x * rpc + g;
+    const bool row_ok = y < a.H;
+    float *Ue = sm + (size_t)g * 3 * line_floats;  // u over [-B, W + A)
+    float *Qe = Ue + line_floats;                  // q over [-A, W + B)
+    float *Fr = Qe + line_floats;                  // f over [0, W)
+    uint8_t *Mk = reinterpret_cast<uint8_t *>(sm + (size_t)rpc * 3 * line_floats) + (size_t)g * mask_bytes;
+    const float w = a.weight;
+    unsigned used = 0;
+
+    if (row_ok) {
+        const T *urow = (const T *)a.u_in + (long long)y * a.in_pitch;
+        row_to_smem<4>(Ue, [B](int i) { return PI(i + B); }, urow, W, t, tpr);
+        row_to_smem<4>(Fr, [](int i) { return PI(i); }, (const T *)a.f + (long long)y * a.f_pitch, W, t, tpr);
+        gather_batched<4>(A + B, t, tpr,
+            [&](int i) { return Stor<T>::ld(urow, bmap(i < B ? i - B : W + i - B, W, a.clamp)); },
+            [&](int i, float v) { Ue[PI(i < B ? i : W + i)] = v; });
+        for (int i = t; i < W + L - 1; i += tpr) Qe[PI(i)] = 0.f;  // stale ratio of a never-used pixel
+        if (THIN)
+            for (int x = t; x < W; x += tpr) Mk[x] = 1;
+    }
+    __syncthreads();
+    for (int k = 0; k < tb.K; ++k) {
+        const bool full = !THIN || (k % tb.P) == 0;
+        const uint8_t *srow = (THIN && tb.sched && row_ok)
+                                  ? tb.sched + (long long)k * tb.s_plane + (long long)y * tb.s_pitch
+                                  : nullptr;
+        if (row_ok) {  // q = f / (h (x) u) at the used pixels
+            for (int x0 = t * XCH; x0 < W; x0 += tpr * XCH) {
+                float s = 0.f;
+                for (int kk = 0; kk < L; ++kk) s += Ue[PI(x0 + kk)];
+#pragma unroll
+                for (int j = 0; j < XCH; ++j) {
+                    const int x = x0 + j;
+                    if (x < W) {
+                        bool use = true;
+                        if (THIN) use = srow ? srow[x] != 0 : (full || Mk[x] != 0);
+                        if (use) put_continued(Qe, A, x, rl_ratio(Fr[PI(x)], s * w), W, A, B, a.clamp);
+                        if (j + 1 < XCH && x + 1 < W) s += Ue[PI(x + L)] - Ue[PI(x)];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (row_ok) {  // c = h* (x) q, u' = u c
+            for (int x0 = t * XCH; x0 < W; x0 += tpr * XCH) {
+                float s = 0.f;
+                for (int kk = 0; kk < L; ++kk) s += Qe[PI(x0 + kk)];
+#pragma unroll
+                for (int j = 0; j < XCH; ++j) {
+                    const int x = x0 + j;
+                    if (x < W) {
+                        const float u = Ue[PI(x + B)];
+                        const float c = s * w;
+                        float un = u * c;
+                        if (THIN) {
+                            const bool use = srow ? srow[x] != 0 : (full || Mk[x] != 0);
+                            used += use;
+                            if (!use) un = u;
+                            if (!srow && (tb.Q == 1 || full)) {
+                                float d = 0.f;
+                                if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
+                                Mk[x] = (uint8_t)(use && d >= a.tau);
+                            }
+                        }
+                        if (tb.round) un = Stor<T>::round(un);
+                        if (j + 1 < XCH && x + 1 < W) s += Qe[PI(x + L)] - Qe[PI(x)];
+                        put_continued(Ue, B, x, un, W, B, A, a.clamp);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (row_ok) {
+        smem_to_row((T *)a.u_out + (long long)y * a.out_pitch, Ue, [B](int i) { return PI(i + B); }, W, t, tpr);
+        if (THIN && !tb.sched && a.mask_out)
+            for (int x = t; x < W; x += tpr) a.mask_out[(long long)y * a.m_pitch + x] = Mk[x];
+    }
+    if (THIN && a.active_count) warp_count_add(a.active_count, used);
+}
+
+template <typename T, bool THIN>
+cudaError_t launch_x_tb_t(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
+    const int L = a.ax + a.bx + 1;
+    const int chunks = (a.W + XCH - 1) / XCH;
+    int tpr = ((chunks + 31) / 32) * 32;
+    if (tpr > 256) tpr = 256;
+    const int rpc = 256 / tpr;
+    const int n_ext = a.W + L - 1;
+    const int line_floats = ((n_ext + (n_ext >> 5) + 1) + 3) & ~3;
+    const int mask_bytes = THIN ? (a.W + 15) & ~15 : 0;
+    const size_t smem = (size_t)rpc * (3 * line_floats * sizeof(float) + mask_bytes);
+    cudaError_t e = ensure_smem<k_motion_x_tb<T, THIN>>(smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.H + rpc - 1) / rpc);
+    k_motion_x_tb<T, THIN><<<grid, tpr * rpc, smem, s>>>(a, tb, tpr, rpc, line_floats, mask_bytes);
+    return cudaGetLastError();
+}
+
 template <typename T, bool THIN>
 cudaError_t launch_x_t(const IterArgs &a, cudaStream_t s) {
     const int L = a.ax + a.bx + 1;
@@ -231,6 +361,29 @@ cudaError_t launch_y_t(const IterArgs &a, cudaStream_t s) {
 }
 
 }  // namespace
+
+size_t motion_x_tb_smem_bytes(int W, int L, bool thin) {
+    const int n_ext = W + L - 1;
+    const int line_floats = ((n_ext + (n_ext >> 5) + 1) + 3) & ~3;
+    const int chunks = (W + XCH - 1) / XCH;
+    int tpr = ((chunks + 31) / 32) * 32;
+    if (tpr > 256) tpr = 256;
+    const int mask_bytes = thin ? (W + 15) & ~15 : 0;
+    return (size_t)(256 / tpr) * (3 * line_floats * sizeof(float) + mask_bytes);
+}
+
+bool motion_x_tb_fits(int W, int L, bool thin) { return motion_x_tb_smem_bytes(W, L, thin) <= 200 * 1024; }
+
+cudaError_t launch_motion_x_tb(const IterArgs &a, const TBArgs &tb, int storage, bool thin,
+                               cudaStream_t s) {
+    switch (storage) {
+    case ST_F32: return thin ? launch_x_tb_t<float, true>(a, tb, s) : launch_x_tb_t<float, false>(a, tb, s);
+    case ST_BF16: return thin ? launch_x_tb_t<__nv_bfloat16, true>(a, tb, s)
+                              : launch_x_tb_t<__nv_bfloat16, false>(a, tb, s);
+    case ST_F16: return thin ? launch_x_tb_t<__half, true>(a, tb, s) : launch_x_tb_t<__half, false>(a, tb, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 size_t motion_x_smem_bytes(int W, int L) {
     const int n_ext = W + L - 1;

@@ -26,6 +26,8 @@ struct rl_ctx {
     int storage = RL_STORAGE_F32;
     int boundary = RL_BOUNDARY_MIRROR;
     int path_pref = RL_PATH_AUTO;
+    int flags = 0;
+    int launches = 0;  // kernel launches issued by the current rl_iterate call
     std::string err;
 
     // PSF plan
@@ -47,6 +49,10 @@ struct rl_ctx {
     size_t thin_px = 0;
     float *qplane = nullptr;  // ratio plane of the two-launch disc path
     size_t q_px = 0;
+    void *tbuf[2] = {nullptr, nullptr};  // transposed f and u (motion along y)
+    size_t tbuf_bytes = 0;
+    void *tsched = nullptr;              // transposed schedule / mask bytes
+    size_t tsched_bytes = 0;
     unsigned long long *d_counter = nullptr;
     void *stage[3] = {nullptr, nullptr, nullptr};
     size_t stage_bytes[3] = {0, 0, 0};
@@ -119,7 +125,7 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
         return RL_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    rl_config c = {0, nullptr, RL_STORAGE_F32, RL_BOUNDARY_MIRROR, RL_PATH_AUTO};
+    rl_config c = {0, nullptr, RL_STORAGE_F32, RL_BOUNDARY_MIRROR, RL_PATH_AUTO, 0};
     if (cfg) c = *cfg;
     if (c.storage < RL_STORAGE_F32 || c.storage > RL_STORAGE_F16 ||
         (c.boundary != RL_BOUNDARY_MIRROR && c.boundary != RL_BOUNDARY_CLAMP) ||
@@ -156,6 +162,7 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
     ctx->storage = c.storage;
     ctx->boundary = c.boundary;
     ctx->path_pref = c.path;
+    ctx->flags = c.flags;
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
@@ -186,6 +193,9 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->mask[1]);
     cudaFree(ctx->rstale);
     cudaFree(ctx->qplane);
+    cudaFree(ctx->tbuf[0]);
+    cudaFree(ctx->tbuf[1]);
+    cudaFree(ctx->tsched);
     cudaFree(ctx->d_counter);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
     cudaFree(ctx->sched);
@@ -324,6 +334,124 @@ int choose_path(const rl_ctx *ctx, int W) {
     return p;
 }
 
+// All K iterations of the running-sum path in one launch of the row-resident
+// kernel.  Motion along y runs on the transposed image (transposed f, start,
+// schedule in; transposed result and mask out).
+rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_out, int W, int H,
+                       long long pitch, int K, const rl_thinning *thin, size_t plane, long long sp) {
+    const size_t es = elem_size(ctx->storage);
+    IterArgs a;
+    memset(&a, 0, sizeof a);
+    a.clamp = ctx->boundary == RL_BOUNDARY_CLAMP;
+    a.weight = ctx->weight;
+    rl::TBArgs tb;
+    memset(&tb, 0, sizeof tb);
+    tb.K = K;
+    tb.round = ctx->storage != RL_STORAGE_F32;
+    const bool ydir = ctx->axis == 1;
+    const int Wt = ydir ? H : W, Ht = ydir ? W : H;   // the problem the kernel sees
+    const long long tp = ((long long)Wt + 63) / 64 * 64;
+    if (thin) {
+        tb.P = thin->reset_period;
+        tb.Q = thin->update_period;
+        a.relative = thin->relative != 0;
+        a.tau = thin->threshold;
+        a.active_count = ctx->d_counter;
+        a.mask_out = ydir ? nullptr : ctx->mask[0];
+        a.m_pitch = sp;
+    }
+    const uint8_t *sched = nullptr;
+    if (thin && thin->schedule) {
+        const size_t bytes = (size_t)W * H * K;
+        if (is_device_ptr(thin->schedule)) {
+            sched = thin->schedule;
+        } else {
+            rl_status st = grow(ctx, &ctx->sched, &ctx->sched_bytes, bytes, "rl_iterate: schedule");
+            if (st != RL_OK) return st;
+            CK(cudaMemcpyAsync(ctx->sched, thin->schedule, bytes, cudaMemcpyHostToDevice, ctx->stream),
+               "rl_iterate: schedule upload");
+            sched = (const uint8_t *)ctx->sched;
+        }
+    }
+    if (!ydir) {
+        a.f = f;
+        a.u_in = start;
+        a.u_out = u_out;
+        a.W = W;
+        a.H = H;
+        a.f_pitch = a.in_pitch = a.out_pitch = pitch;
+        a.ax = ctx->ax;
+        a.bx = ctx->kw - 1 - ctx->ax;
+        if (sched) {
+            tb.sched = sched;
+            tb.s_pitch = W;
+            tb.s_plane = (long long)W * H;
+        }
+        cudaError_t e = rl::launch_motion_x_tb(a, tb, ctx->storage, thin != nullptr, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
+        ctx->launches += 1;
+    } else {
+        const size_t tbytes = (size_t)Ht * tp * es;
+        if (ctx->tbuf_bytes < tbytes) {
+            cudaFree(ctx->tbuf[0]);
+            cudaFree(ctx->tbuf[1]);
+            ctx->tbuf[0] = ctx->tbuf[1] = nullptr;
+            ctx->tbuf_bytes = 0;
+            CK(cudaMalloc(&ctx->tbuf[0], tbytes), "rl_iterate: transposed f");
+            CK(cudaMalloc(&ctx->tbuf[1], tbytes), "rl_iterate: transposed u");
+            ctx->tbuf_bytes = tbytes;
+        }
+        CK(rl::launch_transpose(f, pitch, 0, ctx->tbuf[0], tp, 0, W, H, 1, (int)es, ctx->stream),
+           "rl_iterate: transpose f");
+        CK(rl::launch_transpose(start, pitch, 0, ctx->tbuf[1], tp, 0, W, H, 1, (int)es, ctx->stream),
+           "rl_iterate: transpose u0");
+        ctx->launches += 2;
+        a.f = ctx->tbuf[0];
+        a.u_in = ctx->tbuf[1];
+        a.u_out = ctx->tbuf[1];
+        a.W = Wt;
+        a.H = Ht;
+        a.f_pitch = a.in_pitch = a.out_pitch = tp;
+        a.ax = ctx->ay;
+        a.bx = ctx->kh - 1 - ctx->ay;
+        const size_t sbytes = thin ? (size_t)Ht * tp * (sched ? (size_t)K : 1) : 0;
+        if (thin) {
+            rl_status st = grow(ctx, &ctx->tsched, &ctx->tsched_bytes, sbytes, "rl_iterate: transposed mask");
+            if (st != RL_OK) return st;
+        }
+        if (sched) {
+            CK(rl::launch_transpose(sched, W, (long long)W * H, ctx->tsched, tp, (long long)Ht * tp, W, H,
+                                    K, 1, ctx->stream),
+               "rl_iterate: transpose schedule");
+            ctx->launches += 1;
+            tb.sched = (const uint8_t *)ctx->tsched;
+            tb.s_pitch = tp;
+            tb.s_plane = (long long)Ht * tp;
+        } else if (thin) {
+            a.mask_out = (uint8_t *)ctx->tsched;
+            a.m_pitch = tp;
+        }
+        cudaError_t e = rl::launch_motion_x_tb(a, tb, ctx->storage, thin != nullptr, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
+        CK(rl::launch_transpose(ctx->tbuf[1], tp, 0, u_out, pitch, 0, Wt, Ht, 1, (int)es, ctx->stream),
+           "rl_iterate: transpose back");
+        ctx->launches += 2;
+        if (thin && !sched) {
+            CK(rl::launch_transpose(ctx->tsched, tp, 0, ctx->mask[0], sp, 0, Wt, Ht, 1, 1, ctx->stream),
+               "rl_iterate: transpose mask");
+            ctx->launches += 1;
+        }
+    }
+    if (thin && !sched) {
+        ctx->last_mask = ctx->mask[0];
+        ctx->last_W = W;
+        ctx->last_H = H;
+        ctx->last_mp = sp;
+    }
+    (void)plane;
+    return RL_OK;
+}
+
 rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W, int H,
                      long long pitch, int K, const rl_thinning *thin, int *path_out) {
     const size_t es = elem_size(ctx->storage);
@@ -339,15 +467,6 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     }
     const long long sp = ((long long)W + 63) / 64 * 64;  // scratch pitch (elements)
     const size_t plane = (size_t)sp * H;
-    if ((K > 1 || u_out == start) && ctx->ubuf_bytes < plane * es) {
-        cudaFree(ctx->ubuf[0]);
-        cudaFree(ctx->ubuf[1]);
-        ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
-        ctx->ubuf_bytes = 0;
-        CK(cudaMalloc(&ctx->ubuf[0], plane * es), "rl_iterate: scratch u");
-        CK(cudaMalloc(&ctx->ubuf[1], plane * es), "rl_iterate: scratch u");
-        ctx->ubuf_bytes = plane * es;
-    }
     if (thin) {
         if (ctx->thin_px < plane) {
             for (int i = 0; i < 2; ++i) {
@@ -367,6 +486,22 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
            "rl_iterate: counter");
         // the stale ratio of a pixel that was never used is 0
         CK(cudaMemsetAsync(ctx->rstale, 0, plane * sizeof(float), ctx->stream), "rl_iterate: stale ratio");
+    }
+    // Running sum with whole lines resident for all iterations: one launch.
+    if (path == RL_PATH_RUNSUM && !(ctx->flags & RL_FLAG_PER_ITERATION)) {
+        const int L = ctx->axis == 0 ? ctx->kw : ctx->kh;
+        const int line = ctx->axis == 0 ? W : H;
+        if (rl::motion_x_tb_fits(line, L, thin != nullptr))
+            return run_resident(ctx, f, start, u_out, W, H, pitch, K, thin, plane, sp);
+    }
+    if ((K > 1 || u_out == start) && ctx->ubuf_bytes < plane * es) {
+        cudaFree(ctx->ubuf[0]);
+        cudaFree(ctx->ubuf[1]);
+        ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
+        ctx->ubuf_bytes = 0;
+        CK(cudaMalloc(&ctx->ubuf[0], plane * es), "rl_iterate: scratch u");
+        CK(cudaMalloc(&ctx->ubuf[1], plane * es), "rl_iterate: scratch u");
+        ctx->ubuf_bytes = plane * es;
     }
     const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
                            ctx->disc_radius <= rl::kDiscMaxRadius;
@@ -449,6 +584,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             e = rl::launch_tile(a, ctx->storage, thin != nullptr,
                                 path == RL_PATH_SPAN ? rl::TILE_SPAN : rl::TILE_STENCIL, ts, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
+        ctx->launches += disc_fast ? 2 : 1;
         if (thin && a.update_mask) cur ^= 1;
         if (thin && !sched) {
             ctx->last_mask = ctx->mask[cur];
@@ -521,6 +657,7 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
         du = u0 ? ctx->stage[1] : nullptr;
         dout = ctx->stage[2];
     }
+    ctx->launches = 0;
     if (stats) CK(cudaEventRecord(ctx->ev0, ctx->stream), "rl_iterate: event");
     int path = 0;
     rl_status st = run_device(ctx, df, du, dout, W, H, dp, iterations, thin, &path);
@@ -542,6 +679,7 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
         stats->active_pixel_iterations = (long long)act;
         stats->device_ms = ms;
         stats->path = path;
+        stats->launches = ctx->launches;
     } else if (staged) {
         CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: sync");
     }

@@ -19,16 +19,19 @@ template <> struct Stor<float> {
     static __device__ __forceinline__ float ld(const float *p, long long i) { return __ldg(p + i); }
     static __device__ __forceinline__ float ldc(const float *p, long long i) { return p[i]; }
     static __device__ __forceinline__ void st(float *p, long long i, float v) { p[i] = v; }
+    static __device__ __forceinline__ float round(float v) { return v; }
 };
 template <> struct Stor<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, long long i) { return __bfloat162float(__ldg(p + i)); }
     static __device__ __forceinline__ float ldc(const __nv_bfloat16 *p, long long i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 template <> struct Stor<__half> {
     static __device__ __forceinline__ float ld(const __half *p, long long i) { return __half2float(__ldg(p + i)); }
     static __device__ __forceinline__ float ldc(const __half *p, long long i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void st(__half *p, long long i, float v) { p[i] = __float2half_rn(v); }
+    static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
 };
 
 // 16-byte vectors of a storage type: VEC elements per 16-byte load/store.
@@ -158,6 +161,15 @@ __device__ __forceinline__ void gather_batched(int n, int t, int nt, LD ld, ST s
     }
 }
 
+// Asynchronous 4-byte global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ---- boundary continuation (Sec. 2) ----------------------------------------
 // clamp = closest image pixel; mirror = half-sample symmetric, 2n-periodic.
 __device__ __forceinline__ int bmap(int e, int n, int clamp) {
@@ -197,6 +209,17 @@ struct IterArgs {
     int relative;                            // |c-1| (1) or |u'-u| (0)
     float tau;                               // threshold (strict < -> inactive)
     unsigned long long *active_count;        // += used pixels (nullable)
+};
+
+// Several iterations in one launch (kernels that keep their lines resident).
+struct TBArgs {
+    int K;                  // iterations
+    int P;                  // reset period of selective convolution (full when k % P == 0)
+    int Q;                  // mask update period: 1 or P
+    const uint8_t *sched;   // replayed used-pixel masks, K planes (nullable)
+    long long s_pitch;      // row pitch of a schedule plane (bytes)
+    long long s_plane;      // bytes per schedule plane
+    int round;              // round u to the storage type after every iteration
 };
 
 // Ratio f / v of Eq. 3 with q = 0 where the re-blurred value vanishes.

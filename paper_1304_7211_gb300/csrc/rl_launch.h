@@ -17,6 +17,19 @@ cudaError_t launch_motion_x(const IterArgs &a, int storage, bool thin, cudaStrea
 size_t motion_x_smem_bytes(int W, int L);
 bool motion_x_fits(int W, int L);
 
+// Running-sum box filter along x with the rows resident in shared memory for
+// all tb.K iterations (one launch per rl_iterate call).
+cudaError_t launch_motion_x_tb(const IterArgs &a, const TBArgs &tb, int storage, bool thin,
+                               cudaStream_t s);
+size_t motion_x_tb_smem_bytes(int W, int L, bool thin);
+bool motion_x_tb_fits(int W, int L, bool thin);
+
+// Transpose n_planes planes of W x H elements of `elem_bytes` (4, 2 or 1)
+// from src (pitch sp elements) to dst (H x W, pitch dp elements).
+cudaError_t launch_transpose(const void *src, long long sp, long long s_plane, void *dst,
+                             long long dp, long long d_plane, int W, int H, int n_planes,
+                             int elem_bytes, cudaStream_t s);
+
 // Running-sum box filter along y: column strips streamed through shared
 // memory, one fused RL iteration.
 cudaError_t launch_motion_y(const IterArgs &a, int storage, bool thin, cudaStream_t s);

@@ -49,15 +49,19 @@ class rl_thinning(ctypes.Structure):
                 ("schedule", ctypes.c_void_p)]
 
 
+RL_FLAG_PER_ITERATION = 1
+
+
 class rl_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("storage", ctypes.c_int), ("boundary", ctypes.c_int), ("path", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("boundary", ctypes.c_int), ("path", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 class rl_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_longlong), ("pixel_iterations", ctypes.c_longlong),
                 ("active_pixel_iterations", ctypes.c_longlong), ("device_ms", ctypes.c_double),
-                ("path", ctypes.c_int)]
+                ("path", ctypes.c_int), ("launches", ctypes.c_int)]
 
 
 class RLError(RuntimeError):
@@ -117,13 +121,14 @@ def _check(rc: int, ctx) -> None:
         raise RLError(rc, rl_last_error(ctx))
 
 
-def rl_create(device: int = 0, stream=None, storage="f32", boundary="mirror", path="auto"):
+def rl_create(device: int = 0, stream=None, storage="f32", boundary="mirror", path="auto",
+              flags: int = 0):
     """Create a context; ``stream`` is a ``cudaStream_t`` as int, a
     ``torch.cuda.Stream`` or None (default stream)."""
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     cfg = rl_config(device, stream or None, STORAGE.get(storage, storage),
-                    BOUNDARY.get(boundary, boundary), PATH.get(path, path))
+                    BOUNDARY.get(boundary, boundary), PATH.get(path, path), flags)
     h = ctypes.c_void_p()
     rc = load().rl_create(ctypes.byref(cfg), ctypes.byref(h))
     _check(rc, None)
@@ -223,7 +228,7 @@ class Deconvolver:
     """
 
     def __init__(self, spec, device: int = 0, storage="f32", boundary="mirror",
-                 path="auto", stream=None):
+                 path="auto", stream=None, flags: int = 0):
         self.device = device
         self.storage = storage
         if stream is None:
@@ -233,7 +238,7 @@ class Deconvolver:
                     stream = torch.cuda.current_stream(device).cuda_stream
             except Exception:  # pragma: no cover - torch is optional here
                 stream = None
-        self.ctx = rl_create(device, stream, storage, boundary, path)
+        self.ctx = rl_create(device, stream, storage, boundary, path, flags)
         rl_set_psf(self.ctx, spec)
 
     def close(self):

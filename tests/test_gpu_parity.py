@@ -345,3 +345,55 @@ def test_thinned_free_running_masks(spec, path, relative, tau, q):
     assert dis <= 0.005 * mask.size
     assert act_rel <= 0.005
     assert err <= 1e-2
+
+
+# ---- running sum: whole rows resident vs one launch per iteration -------------
+
+def run_flags(spec, f32, iters, flags, boundary="mirror", storage="f32", thin=None):
+    from paper_1304_7211_gb300 import rl
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[storage]
+    f = torch.from_numpy(f32).cuda().to(dt)
+    with rl.Deconvolver(spec, storage=storage, boundary=boundary, path="runsum", flags=flags) as d:
+        u, st = d.run(f, iters, thin=thin, stats=True)
+        m = d.mask() if thin is not None and thin.schedule is None else None
+    torch.cuda.synchronize()
+    return u.float().cpu().numpy(), st, m
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("boundary", ["mirror", "clamp"])
+@pytest.mark.parametrize("spec", [synth.motion(15, 0), synth.motion(8, 0), synth.motion(15, 1),
+                                  synth.motion(8, 1)], ids=lambda s: s.name)
+def test_resident_rows_match_per_iteration(spec, boundary, storage):
+    from paper_1304_7211_gb300 import rl
+    f32 = case(203, 157, spec, seed=synth.SEED_BASE + 53)
+    res, _, _ = run_flags(spec, f32, 23, 0, boundary, storage)
+    per, _, _ = run_flags(spec, f32, 23, rl.RL_FLAG_PER_ITERATION, boundary, storage)
+    if spec.axis == 0:
+        np.testing.assert_array_equal(res, per)  # same arithmetic, same order
+    else:
+        tol = 1e-5 if storage == "f32" else 23 * UNIT_ROUNDOFF["bf16"]
+        assert oracle.rel_linf(res, per) <= tol
+
+
+@pytest.mark.parametrize("q", [1, 10])
+@pytest.mark.parametrize("spec", [synth.motion(15, 0), synth.motion(15, 1)], ids=lambda s: s.name)
+def test_resident_rows_thinning(spec, q):
+    from paper_1304_7211_gb300 import rl
+    f32 = case(170, 150, spec, seed=synth.SEED_BASE + 52)
+    th = rl.thinning(1e-3, update_period=q)
+    res, st_r, m_r = run_flags(spec, f32, 34, 0, thin=th)
+    per, st_p, m_p = run_flags(spec, f32, 34, rl.RL_FLAG_PER_ITERATION, thin=th)
+    if spec.axis == 0:
+        np.testing.assert_array_equal(res, per)
+        np.testing.assert_array_equal(m_r, m_p)
+        assert st_r.active_pixel_iterations == st_p.active_pixel_iterations
+    else:
+        assert int(np.sum(m_r != m_p)) <= 0.005 * m_r.size
+    # replay of the oracle's schedule through the resident kernel
+    resq = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 34, threshold=1e-3,
+                     update_period=q, want_mask=True)
+    th2 = rl.thinning(1e-3, update_period=q, schedule=np.ascontiguousarray(resq.mask_trace))
+    rep, st, _ = run_flags(spec, f32, 34, 0, thin=th2)
+    assert oracle.rel_linf(rep, resq.u) <= TOL
+    assert st.active_pixel_iterations == resq.active_pixel_iterations
