@@ -30,7 +30,8 @@ constexpr int SX = 8;  // outputs per thread along x
 constexpr int SY = 4;  // outputs per thread along y
 
 // Shared-memory column with one skew word every SX columns: a warp's 4 x 8
-// patch of blocks then reads 32 distinct banks (odd row pitch).
+// patch of blocks (4 across, 8 down) then reads 32 distinct banks (odd row
+// pitch).
 __device__ __forceinline__ int sk(int c) { return c + (c >> 3); }
 
 // Half-width of the disc's run in PSF row ty: largest s with s^2 + ty^2 <= R^2.
@@ -54,6 +55,25 @@ __device__ __forceinline__ void stage_rows(float *dst, int pitch, int nrows, int
                                            int c_lo, int c_hi, bool inside, int clamp, int W,
                                            int H, int y0, int x0, const T *src, long long sp,
                                            int wid, int nwarps, int lane, int r_lo = 0) {
+    if constexpr (sizeof(T) == 4) {
+        // FP32: asynchronous global -> shared copies, all of a thread's copies
+        // in flight at once; the caller waits (cp_async_wait_all) before the barrier.
+        for (int r = wid; r < nrows; r += nwarps) {
+            const bool row_in = r >= r_lo && r < r_hi;
+            const int yy = row_in ? (inside ? y0 + r : bmap(y0 + r, H, clamp)) : 0;
+            const float *srow = reinterpret_cast<const float *>(src) + (long long)yy * sp;
+            float *drow = dst + r * pitch;
+            for (int c = lane; c < ncols; c += 32) {
+                if (row_in && c >= c_lo && c < c_hi) {
+                    const int xx = inside ? x0 + c : bmap(x0 + c, W, clamp);
+                    cp_async4(drow + sk(c), srow + xx);
+                } else {
+                    drow[sk(c)] = 0.f;
+                }
+            }
+        }
+        return;
+    }
     constexpr int RB = 4;
     for (int rb = wid * RB; rb < nrows; rb += nwarps * RB) {
         for (int cb = lane; cb < ncols; cb += 32) {
@@ -85,18 +105,28 @@ template <int R>
 __device__ __forceinline__ void disc_block(const float *src, int pitch, int row0, int colblk,
                                            float (&acc)[SY][SX]) {
     constexpr int NW = SX + 2 * R;
+    constexpr int NR = SY + 2 * R;
 #pragma unroll
     for (int i = 0; i < SY; ++i)
 #pragma unroll
         for (int j = 0; j < SX; ++j) acc[i][j] = 0.f;
     const float *base = src + row0 * pitch + colblk * (SX + 1);
+    // The window of the next input row is loaded while the current one is
+    // summed, so shared-memory latency overlaps the additions.
+    float w[NW];
 #pragma unroll
-    for (int m = 0; m < SY + 2 * R; ++m) {
-        const float *rp = base + m * pitch;
+    for (int k = 0; k < NW; ++k) w[k] = base[k + (k >> 3)];
+#pragma unroll
+    for (int m = 0; m < NR; ++m) {
+        float wn[NW];
+        if (m + 1 < NR) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) wn[k] = base[(m + 1) * pitch + k + (k >> 3)];
+        }
         float P[NW + 1];
         P[0] = 0.f;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) P[k + 1] = P[k] + rp[k + (k >> 3)];
+        for (int k = 0; k < NW; ++k) P[k + 1] = P[k] + w[k];
 #pragma unroll
         for (int i = 0; i < SY; ++i) {
             const int ty = i + R - m;
@@ -105,33 +135,38 @@ __device__ __forceinline__ void disc_block(const float *src, int pitch, int row0
 #pragma unroll
             for (int j = 0; j < SX; ++j) acc[i][j] += P[j + R + 1 + s] - P[j + R - s];
         }
+        if (m + 1 < NR) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) w[k] = wn[k];
+        }
     }
 }
 
-// One half of an RL iteration for a TILE x TILE output tile (128 threads, one
+// One half of an RL iteration for a TX x TY output tile (128 threads, one
 // SY x SX block each).  FWD: v = h (x) u and q = f / v on the tile, written
 // to the q plane (inactive pixels keep their q: it is the ratio of their last
 // active iteration, Eq. 5).  !FWD: c = h* (x) q and u' = u c with the
 // selective-convolution bookkeeping.  The input plane (u or q) is staged with
 // a 2R halo continued across the image border.
-constexpr int TILE = 64;
+constexpr int TX = 64, TY = 64;
 
 template <typename T, bool THIN, int R, bool FWD>
 __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane, long long q_pitch) {
     extern __shared__ float sm[];
-    constexpr int NS = TILE + 2 * R;           // staged rows and columns
-    constexpr int SP = (NS + (NS >> 3)) | 1;   // skewed, odd pitch
-    const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+    constexpr int NSX = TX + 2 * R, NSY = TY + 2 * R;  // staged columns and rows
+    constexpr int SP = (NSX + (NSX >> 3)) | 1;         // skewed, odd pitch
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
     {
-        const bool inside = x0 - R >= 0 && x0 + TILE + R <= a.W && y0 - R >= 0 && y0 + TILE + R <= a.H;
+        const bool inside = x0 - R >= 0 && x0 + TX + R <= a.W && y0 - R >= 0 && y0 + TY + R <= a.H;
         if (FWD)
-            stage_rows<T>(sm, SP, NS, NS, NS, 0, NS, inside, a.clamp, a.W, a.H, y0 - R, x0 - R,
+            stage_rows<T>(sm, SP, NSY, NSX, NSY, 0, NSX, inside, a.clamp, a.W, a.H, y0 - R, x0 - R,
                           (const T *)a.u_in, a.in_pitch, wid, 4, lane);
         else
-            stage_rows<float>(sm, SP, NS, NS, NS, 0, NS, inside, a.clamp, a.W, a.H, y0 - R, x0 - R,
-                              qplane, q_pitch, wid, 4, lane);
+            stage_rows<float>(sm, SP, NSY, NSX, NSY, 0, NSX, inside, a.clamp, a.W, a.H, y0 - R,
+                              x0 - R, qplane, q_pitch, wid, 4, lane);
+        cp_async_wait_all();
     }
     __syncthreads();
     // warp w covers the 32 x 32 quarter (w & 1, w >> 1); lane = 4 (x) x 8 (y) blocks
@@ -177,9 +212,9 @@ __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane,
 
 template <int R>
 constexpr size_t half_smem_bytes() {
-    constexpr int NS = TILE + 2 * R;
-    constexpr int SP = (NS + (NS >> 3)) | 1;
-    return (size_t)NS * SP * sizeof(float);
+    constexpr int NSX = TX + 2 * R, NSY = TY + 2 * R;
+    constexpr int SP = (NSX + (NSX >> 3)) | 1;
+    return (size_t)NSY * SP * sizeof(float);
 }
 
 template <int R, typename T, bool THIN>
@@ -188,7 +223,7 @@ cudaError_t launch_one(const IterArgs &a, float *qplane, long long q_pitch, cuda
     cudaError_t e = ensure_smem<k_disc_half<T, THIN, R, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, R, false>>(smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.W + TILE - 1) / TILE, (a.H + TILE - 1) / TILE);
+    dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY);
     k_disc_half<T, THIN, R, true><<<grid, 128, smem, s>>>(a, qplane, q_pitch);
     k_disc_half<T, THIN, R, false><<<grid, 128, smem, s>>>(a, qplane, q_pitch);
     return cudaGetLastError();
