@@ -173,15 +173,19 @@ def run_case(args):
     spec = specs[args.case]
     g = synth.latent_image(args.size, args.size, synth.SEED_BASE + 2)
     f32 = np.maximum(synth.blur(g, spec), 0.0).astype(np.float32)
-    f = torch.from_numpy(f32).cuda()
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.storage]
+    f = torch.from_numpy(f32).cuda().to(dt)
     u = torch.empty_like(f)
-    with rl.Deconvolver(spec, path=args.path) as d:
-        rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters)
+    th = None if args.tau is None else rl.thinning(args.tau, True, 10, args.q)
+    with rl.Deconvolver(spec, path=args.path, storage=args.storage) as d:
+        rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th)
         torch.cuda.synchronize()
-        st = rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters,
+        st = rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th,
                            stats=True)
-    print(f"case {spec.name} {args.size}^2 x {args.iters} it: {st.device_ms:.3f} ms "
-          f"({st.device_ms / args.iters * 1e3:.1f} us/it) path={rl.PATH_NAME[st.path]}")
+    act = st.active_pixel_iterations / max(st.pixel_iterations, 1)
+    print(f"case {spec.name} {args.size}^2 x {args.iters} it {args.storage} tau={args.tau}: "
+          f"{st.device_ms:.3f} ms ({st.device_ms / args.iters * 1e3:.1f} us/it) "
+          f"path={rl.PATH_NAME[st.path]} active={100 * act:.1f}% launches={st.launches}")
     return 0
 
 
@@ -198,6 +202,9 @@ def main():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--path", default="auto")
+    ap.add_argument("--tau", type=float, default=None, help="case mode: relative thinning threshold")
+    ap.add_argument("--q", type=int, default=10, help="case mode: mask update period (1 or 10)")
+    ap.add_argument("--storage", default="f32")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -74,26 +74,32 @@ __device__ __forceinline__ void stage_rows(float *dst, int pitch, int nrows, int
         }
         return;
     }
-    constexpr int RB = 4;
+    // 16-bit storage: loads through registers (converted to FP32), RB rows x
+    // CB column passes in flight per thread.
+    constexpr int RB = 4, CB = 3;
     for (int rb = wid * RB; rb < nrows; rb += nwarps * RB) {
-        for (int cb = lane; cb < ncols; cb += 32) {
-            float v[RB];
-#pragma unroll
-            for (int k = 0; k < RB; ++k) {
-                const int r = rb + k;
-                v[k] = 0.f;
-                if (r < nrows && r >= r_lo && r < r_hi && cb >= c_lo && cb < c_hi) {
-                    int yy = y0 + r, xx = x0 + cb;
-                    if (!inside) {
-                        yy = bmap(yy, H, clamp);
-                        xx = bmap(xx, W, clamp);
-                    }
-                    v[k] = Stor<T>::ld(src, (long long)yy * sp + xx);
-                }
-            }
+        for (int c0 = lane; c0 < ncols; c0 += 32 * CB) {
+            float v[RB][CB];
 #pragma unroll
             for (int k = 0; k < RB; ++k)
-                if (rb + k < nrows) dst[(rb + k) * pitch + sk(cb)] = v[k];
+#pragma unroll
+                for (int q = 0; q < CB; ++q) {
+                    const int r = rb + k, cb = c0 + 32 * q;
+                    v[k][q] = 0.f;
+                    if (r < nrows && cb < ncols && r >= r_lo && r < r_hi && cb >= c_lo && cb < c_hi) {
+                        int yy = y0 + r, xx = x0 + cb;
+                        if (!inside) {
+                            yy = bmap(yy, H, clamp);
+                            xx = bmap(xx, W, clamp);
+                        }
+                        v[k][q] = Stor<T>::ld(src, (long long)yy * sp + xx);
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+#pragma unroll
+                for (int q = 0; q < CB; ++q)
+                    if (rb + k < nrows && c0 + 32 * q < ncols) dst[(rb + k) * pitch + sk(c0 + 32 * q)] = v[k][q];
         }
     }
 }
@@ -158,6 +164,10 @@ __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane,
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
+    // Selective convolution at tile granularity: a tile none of whose pixels
+    // is active does nothing (u stays, q keeps the stale ratios).
+    int *tflag = (THIN && a.tile_flags) ? a.tile_flags + blockIdx.y * a.tiles_x + blockIdx.x : nullptr;
+    if (tflag && !a.full && *tflag == 0) return;
     {
         const bool inside = x0 - R >= 0 && x0 + TX + R <= a.W && y0 - R >= 0 && y0 + TY + R <= a.H;
         if (FWD)
@@ -170,44 +180,96 @@ __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane,
     }
     __syncthreads();
     // warp w covers the 32 x 32 quarter (w & 1, w >> 1); lane = 4 (x) x 8 (y) blocks
-    const int bx = (wid & 1) * 4 + (lane & 3), by = (wid >> 1) * 8 + (lane >> 2);
-    float acc[SY][SX];
-    disc_block<R>(sm, SP, by * SY, bx, acc);
-    const int xb = x0 + bx * SX, yb = y0 + by * SY;
-#pragma unroll
-    for (int i = 0; i < SY; ++i) {
-        const int y = yb + i;
-        if (y >= a.H) break;
-#pragma unroll
-        for (int j = 0; j < SX; ++j) {
-            const int x = xb + j;
-            if (x >= a.W) break;
-            if (FWD) {
-                bool use = true;
-                if (THIN && !a.full) use = a.mask_in[(long long)y * a.mi_pitch + x] != 0;
-                if (use) {
-                    const float fv = Stor<T>::ld((const T *)a.f, (long long)y * a.f_pitch + x);
-                    qplane[(long long)y * q_pitch + x] = rl_ratio(fv, acc[i][j] * a.weight);
+    // Natural block of this thread: warp w covers the 32 x 32 quarter
+    // (w & 1, w >> 1); lane = 4 (x) x 8 (y) blocks.
+    const int nbx = (wid & 1) * 4 + (lane & 3), nby = (wid >> 1) * 8 + (lane >> 2);
+    // Selective convolution: compact the blocks with at least one pixel used
+    // this iteration (warp ballot + prefix over the warps) and convolve only
+    // those; warps left without blocks retire early.
+    int n_active = TX / SX * TY / SY;
+    __shared__ int blist[TX / SX * TY / SY];
+    __shared__ int wcount[4];
+    if (THIN && !a.full) {
+        bool any = false;
+        for (int i = 0; i < SY; ++i) {
+            const int y = y0 + nby * SY + i, x = x0 + nbx * SX;
+            if (y < a.H && x < a.W) {
+                const uint8_t *mrow = a.mask_in + (long long)y * a.mi_pitch + x;
+                if (x + SX <= a.W && ((reinterpret_cast<uintptr_t>(mrow) & 7) == 0)) {
+                    any |= *reinterpret_cast<const unsigned long long *>(mrow) != 0ull;
+                } else {
+                    for (int j = 0; j < SX && x + j < a.W; ++j) any |= mrow[j] != 0;
                 }
-            } else {
-                const float u = Stor<T>::ld((const T *)a.u_in, (long long)y * a.in_pitch + x);
-                const float c = acc[i][j] * a.weight;
-                float un = u * c;
-                if (THIN) {
-                    const bool use = a.full || a.mask_in[(long long)y * a.mi_pitch + x] != 0;
-                    used += use;
-                    un = use ? un : u;
-                    if (a.update_mask && !a.replay) {
-                        float d = 0.f;
-                        if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
-                        a.mask_out[(long long)y * a.m_pitch + x] = (uint8_t)(use && d >= a.tau);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, any);
+        if (lane == 0) wcount[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int k = 0; k < wid; ++k) off += wcount[k];
+        n_active = wcount[0] + wcount[1] + wcount[2] + wcount[3];
+        if (any) blist[off + __popc(bal & ((1u << lane) - 1u))] = nby * (TX / SX) + nbx;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n_active; e += 128) {
+        int bx = nbx, by = nby;
+        if (THIN && !a.full) {
+            const int b = blist[e];
+            bx = b % (TX / SX);
+            by = b / (TX / SX);
+        }
+        const int xb = x0 + bx * SX, yb = y0 + by * SY;
+        float acc[SY][SX];
+        disc_block<R>(sm, SP, by * SY, bx, acc);
+#pragma unroll
+        for (int i = 0; i < SY; ++i) {
+            const int y = yb + i;
+            if (y >= a.H) break;
+#pragma unroll
+            for (int j = 0; j < SX; ++j) {
+                const int x = xb + j;
+                if (x >= a.W) break;
+                if (FWD) {
+                    bool use = true;
+                    if (THIN && !a.full) use = a.mask_in[(long long)y * a.mi_pitch + x] != 0;
+                    if (use) {
+                        const float fv = Stor<T>::ld((const T *)a.f, (long long)y * a.f_pitch + x);
+                        qplane[(long long)y * q_pitch + x] = rl_ratio(fv, acc[i][j] * a.weight);
                     }
+                } else {
+                    const float u = Stor<T>::ld((const T *)a.u_in, (long long)y * a.in_pitch + x);
+                    const float c = acc[i][j] * a.weight;
+                    float un = u * c;
+                    if (THIN) {
+                        const bool use = a.full || a.mask_in[(long long)y * a.mi_pitch + x] != 0;
+                        used += use;
+                        un = use ? un : u;
+                        if (a.update_mask && !a.replay) {
+                            float d = 0.f;
+                            if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
+                            a.mask_out[(long long)y * a.m_pitch + x] = (uint8_t)(use && d >= a.tau);
+                        }
+                    }
+                    Stor<T>::st((T *)a.u_out, (long long)y * a.out_pitch + x, un);
                 }
-                Stor<T>::st((T *)a.u_out, (long long)y * a.out_pitch + x, un);
             }
         }
     }
-    if (!FWD && THIN && a.active_count) warp_count_add(a.active_count, used);
+    const int xb = x0 + nbx * SX, yb = y0 + nby * SY;
+    if (!FWD && THIN) {
+        if (a.active_count) warp_count_add(a.active_count, used);
+        if (tflag && a.update_mask) {
+            // does any pixel of the tile stay active for the next iteration?
+            bool any = false;
+            for (int i = 0; i < SY; ++i)
+                for (int j = 0; j < SX; ++j) {
+                    const int y = yb + i, x = xb + j;
+                    if (y < a.H && x < a.W) any |= a.mask_out[(long long)y * a.m_pitch + x] != 0;
+                }
+            const int n = __syncthreads_count(any);
+            if (threadIdx.x == 0) *tflag = n;
+        }
+    }
 }
 
 template <int R>

@@ -49,6 +49,8 @@ struct rl_ctx {
     size_t thin_px = 0;
     float *qplane = nullptr;  // ratio plane of the two-launch disc path
     size_t q_px = 0;
+    int *tflags = nullptr;    // per-tile activity of the disc path
+    size_t tflags_n = 0;
     void *tbuf[2] = {nullptr, nullptr};  // transposed f and u (motion along y)
     size_t tbuf_bytes = 0;
     void *tsched = nullptr;              // transposed schedule / mask bytes
@@ -193,6 +195,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->mask[1]);
     cudaFree(ctx->rstale);
     cudaFree(ctx->qplane);
+    cudaFree(ctx->tflags);
     cudaFree(ctx->tbuf[0]);
     cudaFree(ctx->tbuf[1]);
     cudaFree(ctx->tsched);
@@ -452,6 +455,103 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
     return RL_OK;
 }
 
+// Disc path: two launches per iteration (forward + ratio, adjoint + update).
+// The adjoint half reads u only at its own pixels, so u and the mask are
+// updated in place in one working buffer; with thinning, tiles with no active
+// pixel skip both launches.
+rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, int W, int H,
+                   long long pitch, int K, const rl_thinning *thin, long long sp) {
+    const size_t es = elem_size(ctx->storage);
+    const size_t plane = (size_t)sp * H;
+    if (ctx->ubuf_bytes < plane * es) {
+        cudaFree(ctx->ubuf[0]);
+        cudaFree(ctx->ubuf[1]);
+        ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
+        ctx->ubuf_bytes = 0;
+        CK(cudaMalloc(&ctx->ubuf[0], plane * es), "rl_iterate: scratch u");
+        CK(cudaMalloc(&ctx->ubuf[1], plane * es), "rl_iterate: scratch u");
+        ctx->ubuf_bytes = plane * es;
+    }
+    IterArgs a;
+    memset(&a, 0, sizeof a);
+    a.f = f;
+    a.W = W;
+    a.H = H;
+    a.f_pitch = pitch;
+    a.clamp = ctx->boundary == RL_BOUNDARY_CLAMP;
+    a.ax = a.bx = a.ay = a.by = ctx->disc_radius;
+    a.weight = ctx->weight;
+    a.m_pitch = a.mi_pitch = sp;
+    const uint8_t *sched = nullptr;
+    if (thin) {
+        a.relative = thin->relative != 0;
+        a.tau = thin->threshold;
+        a.active_count = ctx->d_counter;
+        a.mask_in = ctx->mask[0];
+        a.mask_out = ctx->mask[0];
+        if (thin->schedule) {
+            const size_t bytes = (size_t)W * H * K;
+            if (is_device_ptr(thin->schedule)) {
+                sched = thin->schedule;
+            } else {
+                rl_status st = grow(ctx, &ctx->sched, &ctx->sched_bytes, bytes, "rl_iterate: schedule");
+                if (st != RL_OK) return st;
+                CK(cudaMemcpyAsync(ctx->sched, thin->schedule, bytes, cudaMemcpyHostToDevice, ctx->stream),
+                   "rl_iterate: schedule upload");
+                sched = (const uint8_t *)ctx->sched;
+            }
+        } else {
+            const int tx = (W + 63) / 64, ty = (H + 63) / 64;
+            const size_t n = (size_t)tx * ty;
+            if (ctx->tflags_n < n) {
+                cudaFree(ctx->tflags);
+                ctx->tflags = nullptr;
+                ctx->tflags_n = 0;
+                CK(cudaMalloc(&ctx->tflags, n * sizeof(int)), "rl_iterate: tile flags");
+                ctx->tflags_n = n;
+            }
+            a.tile_flags = ctx->tflags;
+            a.tiles_x = tx;
+        }
+    }
+    void *work = ctx->ubuf[0];
+    for (int k = 0; k < K; ++k) {
+        const bool last = k == K - 1;
+        a.u_in = k == 0 ? start : work;
+        a.in_pitch = k == 0 ? pitch : sp;
+        // without thinning the last iteration writes the caller's buffer
+        const bool direct = last && !thin;
+        a.u_out = direct ? u_out : work;
+        a.out_pitch = direct ? pitch : sp;
+        if (sched) {
+            a.replay = 1;
+            a.full = 0;
+            a.update_mask = 0;
+            a.mask_in = sched + (size_t)k * W * H;
+            a.mi_pitch = W;
+        } else if (thin) {
+            a.full = (k % thin->reset_period) == 0;
+            a.update_mask = thin->update_period == 1 || a.full;
+        }
+        cudaError_t e = rl::launch_disc(a, ctx->storage, thin != nullptr, ctx->disc_radius, ctx->qplane,
+                                        sp, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
+        ctx->launches += 2;
+    }
+    if (thin) {
+        CK(cudaMemcpy2DAsync(u_out, pitch * es, work, sp * es, W * es, H, cudaMemcpyDeviceToDevice,
+                             ctx->stream),
+           "rl_iterate: copy out");
+        if (!sched) {
+            ctx->last_mask = ctx->mask[0];
+            ctx->last_W = W;
+            ctx->last_H = H;
+            ctx->last_mp = sp;
+        }
+    }
+    return RL_OK;
+}
+
 rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W, int H,
                      long long pitch, int K, const rl_thinning *thin, int *path_out) {
     const size_t es = elem_size(ctx->storage);
@@ -514,6 +614,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             ctx->q_px = plane;
         }
         if (thin) CK(cudaMemsetAsync(ctx->qplane, 0, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
+        return run_disc(ctx, f, start, u_out, W, H, pitch, K, thin, sp);
     }
 
     IterArgs a;

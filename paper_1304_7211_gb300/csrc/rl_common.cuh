@@ -209,6 +209,8 @@ struct IterArgs {
     int relative;                            // |c-1| (1) or |u'-u| (0)
     float tau;                               // threshold (strict < -> inactive)
     unsigned long long *active_count;        // += used pixels (nullable)
+    int *tile_flags;                         // per tile: any pixel active next (nullable)
+    int tiles_x;                             // tiles per row of tile_flags
 };
 
 // Several iterations in one launch (kernels that keep their lines resident).
