@@ -209,6 +209,55 @@ rl_status rl_destroy(rl_ctx *ctx);
  * valid until the next call on the same context. */
 const char *rl_last_error(const rl_ctx *ctx);
 
+/*
+ * Batched execution of many independent deconvolutions (the batched and
+ * served workloads): a batch owns `slots` CUDA streams, each with its own
+ * context and scratch.  rl_batch_submit places a job on the slot with the
+ * least queued work (pixel-iterations) and returns at once; jobs on
+ * different slots overlap on the GPU, jobs on one slot run in order.  Each
+ * job's result depends only on its own inputs (no cross-job state), so a job
+ * gives the same image alone and in any mix.
+ *
+ *   f, u0 (NULL = f), u_out: device pointers, caller-owned, valid until the
+ *       job is done; u_out may alias u0 but not f.
+ *   f_host (nullable): pinned or pageable host image uploaded into f on the
+ *       job's stream before it runs.  u_host (nullable): u_out is copied there
+ *       after it runs.  Both use row pitch W elements.
+ *   psf: copied at submit.  thin: nullable, copied at submit (a schedule
+ *       pointer inside must stay valid until the job is done).
+ * Errors: as rl_set_psf / rl_iterate; RL_ERR_INVALID_ARG for a bad ticket.
+ */
+typedef struct {
+    const void *f;
+    const void *u0;
+    void *u_out;
+    const void *f_host;
+    void *u_host;
+    int W, H;
+    long long pitch;
+    int iterations;
+    rl_psf_desc psf;
+    const rl_thinning *thin;
+} rl_job;
+
+typedef struct rl_batch rl_batch;
+
+/* Create a batch of `slots` >= 1 streams on cfg->device (cfg->stream is
+ * ignored: the batch creates its own non-blocking streams). */
+rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out);
+/* Queue a job; *ticket identifies it for rl_batch_query / rl_batch_wait. */
+rl_status rl_batch_submit(rl_batch *b, const rl_job *job, long long *ticket);
+/* *done = 1 when the job's work (and its download) has finished. */
+rl_status rl_batch_query(rl_batch *b, long long ticket, int *done);
+/* Block until the job has finished. */
+rl_status rl_batch_wait(rl_batch *b, long long ticket);
+/* Block until every submitted job has finished. */
+rl_status rl_batch_sync(rl_batch *b);
+/* Wait for all jobs, then release streams, contexts and scratch. NULL-safe. */
+rl_status rl_batch_destroy(rl_batch *b);
+/* Message of the last failure on b. */
+const char *rl_batch_last_error(const rl_batch *b);
+
 /* Library version string, e.g. "rl-gb300 0.1 sm_103a". */
 const char *rl_version(void);
 

@@ -40,6 +40,10 @@ struct rl_ctx {
     float weight = 0.f;                  // the common tap value when uniform
     float *d_taps = nullptr;
     int2 *d_spans = nullptr;
+    size_t taps_cap = 0, spans_cap = 0;
+    char *h_psf = nullptr;        // pinned staging of taps + spans
+    size_t h_psf_cap = 0;
+    cudaEvent_t ev_psf = nullptr; // last PSF upload
 
     // scratch
     void *ubuf[2] = {nullptr, nullptr};
@@ -171,6 +175,7 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
     e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_psf, cudaEventDisableTiming);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         g_create_error = std::string("rl_create: ") + cudaGetErrorString(e);
@@ -202,6 +207,11 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->d_counter);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
     cudaFree(ctx->sched);
+    if (ctx->ev_psf) {
+        cudaEventSynchronize(ctx->ev_psf);
+        cudaEventDestroy(ctx->ev_psf);
+    }
+    if (ctx->h_psf) cudaFreeHost(ctx->h_psf);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     cudaSetDevice(prev);
@@ -287,22 +297,52 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
     std::vector<float> tf(t.size());
     for (size_t k = 0; k < t.size(); ++k) tf[k] = (float)(t[k] / sum);
 
+    // Stream-ordered upload through a pinned staging buffer; device buffers
+    // only grow, so changing the PSF between calls neither allocates nor
+    // synchronises the device (work already queued keeps the old taps).
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
-    cudaFree(ctx->d_taps);
-    cudaFree(ctx->d_spans);
-    ctx->d_taps = nullptr;
-    ctx->d_spans = nullptr;
-    ctx->has_psf = false;
-    cudaError_t e = cudaMalloc(&ctx->d_taps, tf.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_spans, spans.size() * sizeof(int2));
+    const size_t tb = tf.size() * sizeof(float), sb = spans.size() * sizeof(int2);
+    cudaError_t e = cudaSuccess;
+    if (ctx->taps_cap < tb) {
+        cudaFree(ctx->d_taps);
+        ctx->d_taps = nullptr;
+        ctx->taps_cap = 0;
+        e = cudaMalloc(&ctx->d_taps, tb);
+        if (e == cudaSuccess) ctx->taps_cap = tb;
+    }
+    if (e == cudaSuccess && ctx->spans_cap < sb) {
+        cudaFree(ctx->d_spans);
+        ctx->d_spans = nullptr;
+        ctx->spans_cap = 0;
+        e = cudaMalloc(&ctx->d_spans, sb);
+        if (e == cudaSuccess) ctx->spans_cap = sb;
+    }
+    if (e == cudaSuccess && ctx->h_psf_cap < tb + sb) {
+        if (ctx->h_psf) {
+            cudaEventSynchronize(ctx->ev_psf);
+            cudaFreeHost(ctx->h_psf);
+        }
+        ctx->h_psf = nullptr;
+        ctx->h_psf_cap = 0;
+        e = cudaMallocHost((void **)&ctx->h_psf, tb + sb);
+        if (e == cudaSuccess) ctx->h_psf_cap = tb + sb;
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_psf);  // staging buffer free again
+    if (e == cudaSuccess) {
+        memcpy(ctx->h_psf, tf.data(), tb);
+        memcpy(ctx->h_psf + tb, spans.data(), sb);
+        e = cudaMemcpyAsync(ctx->d_taps, ctx->h_psf, tb, cudaMemcpyHostToDevice, ctx->stream);
+    }
     if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->d_taps, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->d_spans, spans.data(), spans.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(ctx->d_spans, ctx->h_psf + tb, sb, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_psf, ctx->stream);
     cudaSetDevice(prev);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_set_psf: upload");
+    if (e != cudaSuccess) {
+        ctx->has_psf = false;
+        return cuda_fail(ctx, e, "rl_set_psf: upload");
+    }
 
     ctx->kind = d->kind;
     ctx->axis = d->kind == RL_PSF_MOTION ? d->axis : 0;

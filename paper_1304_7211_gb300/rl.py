@@ -64,6 +64,13 @@ class rl_stats(ctypes.Structure):
                 ("path", ctypes.c_int), ("launches", ctypes.c_int)]
 
 
+class rl_job(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("u0", ctypes.c_void_p), ("u_out", ctypes.c_void_p),
+                ("f_host", ctypes.c_void_p), ("u_host", ctypes.c_void_p), ("W", ctypes.c_int),
+                ("H", ctypes.c_int), ("pitch", ctypes.c_longlong), ("iterations", ctypes.c_int),
+                ("psf", rl_psf_desc), ("thin", ctypes.POINTER(rl_thinning))]
+
+
 class RLError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAME.get(status, status)}: {message}")
@@ -75,7 +82,9 @@ _lib = None
 
 # Every symbol include/rl.h declares.
 EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error", "rl_version",
-           "rl_get_mask", "rl_motion_x_noalloc")
+           "rl_get_mask", "rl_motion_x_noalloc", "rl_batch_create", "rl_batch_submit",
+           "rl_batch_query", "rl_batch_wait", "rl_batch_sync", "rl_batch_destroy",
+           "rl_batch_last_error")
 RL_NOALLOC_MAX_PIXELS = 4194304
 
 
@@ -104,6 +113,20 @@ def load() -> ctypes.CDLL:
     lib.rl_version.argtypes = []
     lib.rl_get_mask.restype = ctypes.c_int
     lib.rl_get_mask.argtypes = [P, P, ctypes.c_longlong]
+    lib.rl_batch_create.restype = ctypes.c_int
+    lib.rl_batch_create.argtypes = [ctypes.POINTER(rl_config), ctypes.c_int, ctypes.POINTER(P)]
+    lib.rl_batch_submit.restype = ctypes.c_int
+    lib.rl_batch_submit.argtypes = [P, ctypes.POINTER(rl_job), ctypes.POINTER(ctypes.c_longlong)]
+    lib.rl_batch_query.restype = ctypes.c_int
+    lib.rl_batch_query.argtypes = [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+    lib.rl_batch_wait.restype = ctypes.c_int
+    lib.rl_batch_wait.argtypes = [P, ctypes.c_longlong]
+    lib.rl_batch_sync.restype = ctypes.c_int
+    lib.rl_batch_sync.argtypes = [P]
+    lib.rl_batch_destroy.restype = ctypes.c_int
+    lib.rl_batch_destroy.argtypes = [P]
+    lib.rl_batch_last_error.restype = ctypes.c_char_p
+    lib.rl_batch_last_error.argtypes = [P]
     lib.rl_motion_x_noalloc.restype = ctypes.c_int
     lib.rl_motion_x_noalloc.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
@@ -283,3 +306,62 @@ class Deconvolver:
                 out = np.empty_like(f)
         st = rl_iterate(self.ctx, f, u0, out, W, H, pitch, iterations, thin, stats)
         return (out, st) if stats else out
+
+
+class Batch:
+    """Many independent deconvolutions over ``slots`` CUDA streams (the C
+    ``rl_batch_*`` API).  ``submit`` returns a ticket at once; jobs on
+    different slots overlap on the GPU."""
+
+    def __init__(self, slots: int = 8, device: int = 0, storage="f32", boundary="mirror",
+                 path="auto", flags: int = 0):
+        cfg = rl_config(device, None, STORAGE.get(storage, storage),
+                        BOUNDARY.get(boundary, boundary), PATH.get(path, path), flags)
+        h = ctypes.c_void_p()
+        rc = load().rl_batch_create(ctypes.byref(cfg), slots, ctypes.byref(h))
+        if rc != RL_OK:
+            raise RLError(rc, "rl_batch_create failed")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != RL_OK:
+            raise RLError(rc, load().rl_batch_last_error(self.h).decode())
+
+    def submit(self, spec, f, u_out, iterations: int, W: int, H: int, pitch: int | None = None,
+               u0=None, f_host=None, u_host=None, thin: rl_thinning | None = None) -> int:
+        d, keep = psf_desc(spec)
+        job = rl_job(_addr(f), _addr(u0), _addr(u_out), _addr(f_host), _addr(u_host), W, H,
+                     pitch or W, iterations, d,
+                     ctypes.pointer(thin) if thin is not None else None)
+        t = ctypes.c_longlong()
+        self._check(load().rl_batch_submit(self.h, ctypes.byref(job), ctypes.byref(t)))
+        del keep
+        return t.value
+
+    def query(self, ticket: int) -> bool:
+        done = ctypes.c_int()
+        self._check(load().rl_batch_query(self.h, ticket, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, ticket: int) -> None:
+        self._check(load().rl_batch_wait(self.h, ticket))
+
+    def sync(self) -> None:
+        self._check(load().rl_batch_sync(self.h))
+
+    def close(self) -> None:
+        if self.h:
+            load().rl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
