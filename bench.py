@@ -189,6 +189,90 @@ def run_case(args):
     return 0
 
 
+def batch_run(local, n_images=64, slots=8):
+    """Batched workload: 64 images, sides log-uniform in [128, 1536], PSF and
+    iteration count (50..300) per image, all submitted to one rl_batch
+    (8 streams) vs the same solves one at a time.  Returns a dict."""
+    import numpy as np
+    import torch
+    from paper_1304_7211_gb300 import rl, synth
+    dev = torch.device("cuda", local)
+    jobs = []
+    for (w, h, spec, its, seed) in synth.batch_specs(n_images):
+        c = synth.batch_case(w, h, spec, its, seed)
+        f = torch.from_numpy(c.f.astype(np.float32)).to(dev)
+        jobs.append((spec, f, torch.empty_like(f), its, w, h))
+    px_it = float(sum(w * h * its for (_, _, _, its, w, h) in jobs))
+
+    def batched():
+        with rl.Batch(slots, device=local) as b:
+            for spec, f, u, its, w, h in jobs:
+                b.submit(spec, f, u, its, w, h)
+            b.sync()
+
+    def sequential():
+        for spec, f, u, its, w, h in jobs:
+            with rl.Deconvolver(spec, device=local) as d:
+                rl.rl_iterate(d.ctx, f, None, u, w, h, w, its)
+        torch.cuda.synchronize(dev)
+
+    batched()  # warm-up (scratch growth, module load)
+    sequential()
+    ts = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize(dev)
+        ts[name] = time.perf_counter() - t0
+    return {"workload": f"{n_images} images, sides log-uniform [128,1536], motion x/y 5-41, "
+                        f"disc r 3-15, gaussian 7x7; 50-300 it; fp32", "slots": slots,
+            "px_it": px_it, "batched_ms": 1e3 * ts["batched"],
+            "sequential_ms": 1e3 * ts["sequential"],
+            "value": px_it / ts["batched"] / 1e6, "sequential_value": px_it / ts["sequential"] / 1e6,
+            "speedup_vs_plain": ts["sequential"] / ts["batched"], "unit": UNIT,
+            "timing": "host wall clock around submit..sync, inputs resident"}
+
+
+def serve_run(local, n=200, rate=100.0, slots=8):
+    """Served workload: a Poisson-arrival trace (rate req/s), sides
+    log-uniform in [256, 4096], PSF as in the batched workload, 50..500
+    iterations, thinning threshold 1e-4 (mask recomputed every 10
+    iterations), admission under a 150 GB budget; compared with sequential
+    plain solves of the same requests.  Observed images are crops of four
+    pre-blurred 4096^2 images (the request's PSF still drives the solve)."""
+    import numpy as np
+    from paper_1304_7211_gb300 import serve, synth
+    rng = np.random.default_rng(synth.SEED_BASE + 5)
+    bases = {}
+    for k, spec in enumerate((synth.motion(21, 0), synth.motion(21, 1), synth.disc(8),
+                              synth.gaussian(7, 1.5))):
+        bases[k] = synth.make_case(4096, 4096, spec, 0, "poisson", synth.SEED_BASE + 500 + k).f
+    reqs = []
+    for j, (t, w, h, spec, its, seed) in enumerate(synth.serve_trace(n, rate)):
+        fam = {"motion": spec.axis, "disc": 2, "dense": 3}[spec.kind]
+        y0 = int(rng.integers(0, 4096 - h + 1))
+        x0 = int(rng.integers(0, 4096 - w + 1))
+        f = bases[fam][y0:y0 + h, x0:x0 + w].astype(np.float32)
+        reqs.append(serve.Request(j, t, f, spec, its, (1e-4, True, 10, 10)))
+    srv = serve.Server(device=local, slots=slots, hbm_budget_bytes=150e9)
+    try:
+        warm = [serve.Request(-1, 0.0, r.f, r.spec, 5, r.thin) for r in reqs[:8]]
+        srv.run(warm, realtime=False)
+        rep = srv.run(reqs, realtime=True)
+    finally:
+        srv.close()
+    seq_s = serve.sequential(reqs, device=local)
+    d = rep.as_dict()
+    d.update({"rate_per_s": rate, "slots": slots, "unit": UNIT, "value": rep.mpx_it_per_s,
+              "sequential_value": rep.px_it / seq_s / 1e6,
+              "sequential_s": seq_s,
+              "inputs": "crops of 4 pre-blurred 4096^2 images; request PSF drives the solve",
+              "workload": f"{n} requests, Poisson arrivals {rate}/s, sides log-uniform "
+                          f"[256,4096], 50-500 it, thinning 1e-4 (P=Q=10), budget 150 GB"})
+    return d
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +289,9 @@ def main():
     ap.add_argument("--tau", type=float, default=None, help="case mode: relative thinning threshold")
     ap.add_argument("--q", type=int, default=10, help="case mode: mask update period (1 or 10)")
     ap.add_argument("--storage", default="f32")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served sub-measurement")
+    ap.add_argument("--serve-requests", type=int, default=200)
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
@@ -349,6 +436,10 @@ def main():
                     "d2h_bytes_per_step": 3 * plane},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "clocks": clk}
+    if not args.no_batch:
+        line["batch"] = batch_run(local)
+    if not args.no_serve:
+        line["serve"] = serve_run(local, n=args.serve_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(inputs)
     if rank == 0:
