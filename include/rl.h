@@ -145,6 +145,10 @@ typedef struct {
     double device_ms;                 /* stream time of the call (CUDA events) */
     int path;                         /* rl_path that ran                      */
     int launches;                     /* kernel launches the call issued       */
+    double flux_f;                    /* sum of f in FP64 (diagnostics)        */
+    double flux_u;                    /* sum of u_out in FP64; equals flux_f for
+                                         unthinned RL under the mirror boundary
+                                         with an axis-symmetric PSF           */
 } rl_stats;
 
 /*

@@ -44,6 +44,10 @@ struct rl_ctx {
     char *h_psf = nullptr;        // pinned staging of taps + spans
     size_t h_psf_cap = 0;
     cudaEvent_t ev_psf = nullptr; // last PSF upload
+    double *d_flux = nullptr;     // flux_blocks() partials + 2 results
+    // cached CUDA graph of one segment of iterations (see run_segments)
+    cudaGraphExec_t gexec = nullptr;
+    unsigned char gkey[sizeof(rl::IterArgs) + 4 * sizeof(int)] = {};
 
     // scratch
     void *ubuf[2] = {nullptr, nullptr};
@@ -173,6 +177,7 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flux, (rl::flux_blocks() + 2) * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_psf, cudaEventDisableTiming);
@@ -205,6 +210,8 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->tbuf[1]);
     cudaFree(ctx->tsched);
     cudaFree(ctx->d_counter);
+    cudaFree(ctx->d_flux);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
     cudaFree(ctx->sched);
     if (ctx->ev_psf) {
@@ -375,6 +382,55 @@ int choose_path(const rl_ctx *ctx, int W) {
     // Rows too long for shared memory fall back to the span tile kernel.
     if (p == RL_PATH_RUNSUM && ctx->axis == 0 && !rl::motion_x_fits(W, L)) p = RL_PATH_SPAN;
     return p;
+}
+
+// Issue iterations [k0, k1) through a CUDA graph of G consecutive iterations
+// replayed (k1 - k0) / G times; `issue(k)` enqueues iteration k on the
+// context stream and must give the same launches for k and k + G.  The
+// instantiated graph is cached on the context, keyed by the arguments of its
+// first iteration, so repeating an identical call skips the capture.  Returns
+// the first iteration not issued.
+template <typename ISSUE, typename KEYARGS>
+rl_status run_segments(rl_ctx *ctx, int k0, int k1, int G, int extra_key, ISSUE issue,
+                       KEYARGS key_args, int *k_next) {
+    *k_next = k0;
+    const int nseg = G > 0 ? (k1 - k0) / G : 0;
+    if (!ctx->stream || nseg < 2) return RL_OK;
+    unsigned char key[sizeof ctx->gkey];
+    memset(key, 0, sizeof key);
+    const IterArgs ka = key_args(k0);
+    memcpy(key, &ka, sizeof ka);
+    const int meta[4] = {G, extra_key, ctx->storage, ctx->disc_radius};
+    memcpy(key + sizeof ka, meta, sizeof meta);
+    if (!ctx->gexec || memcmp(key, ctx->gkey, sizeof key) != 0) {
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "rl_iterate: capture");
+        rl_status st = RL_OK;
+        const int launches = ctx->launches;
+        for (int k = k0; k < k0 + G && st == RL_OK; ++k) st = issue(k);
+        ctx->launches = launches;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (st != RL_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: capture");
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return cuda_fail(ctx, ei, "rl_iterate: graph instantiate");
+        }
+        memcpy(ctx->gkey, key, sizeof key);
+    }
+    for (int s = 0; s < nseg; ++s)
+        CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "rl_iterate: graph launch");
+    *k_next = k0 + nseg * G;
+    return RL_OK;
 }
 
 // All K iterations of the running-sum path in one launch of the row-resident
@@ -555,28 +611,53 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         }
     }
     void *work = ctx->ubuf[0];
-    for (int k = 0; k < K; ++k) {
+    auto args_for = [&](int k) {
+        IterArgs b = a;
         const bool last = k == K - 1;
-        a.u_in = k == 0 ? start : work;
-        a.in_pitch = k == 0 ? pitch : sp;
+        b.u_in = k == 0 ? start : work;
+        b.in_pitch = k == 0 ? pitch : sp;
         // without thinning the last iteration writes the caller's buffer
         const bool direct = last && !thin;
-        a.u_out = direct ? u_out : work;
-        a.out_pitch = direct ? pitch : sp;
+        b.u_out = direct ? u_out : work;
+        b.out_pitch = direct ? pitch : sp;
         if (sched) {
-            a.replay = 1;
-            a.full = 0;
-            a.update_mask = 0;
-            a.mask_in = sched + (size_t)k * W * H;
-            a.mi_pitch = W;
+            b.replay = 1;
+            b.full = 0;
+            b.update_mask = 0;
+            b.mask_in = sched + (size_t)k * W * H;
+            b.mi_pitch = W;
         } else if (thin) {
-            a.full = (k % thin->reset_period) == 0;
-            a.update_mask = thin->update_period == 1 || a.full;
+            b.full = (k % thin->reset_period) == 0;
+            b.update_mask = thin->update_period == 1 || b.full;
         }
-        cudaError_t e = rl::launch_disc(a, ctx->storage, thin != nullptr, ctx->disc_radius, ctx->qplane,
+        return b;
+    };
+    auto issue = [&](int k) -> rl_status {
+        const IterArgs b = args_for(k);
+        cudaError_t e = rl::launch_disc(b, ctx->storage, thin != nullptr, ctx->disc_radius, ctx->qplane,
                                         sp, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
         ctx->launches += 2;
+        return RL_OK;
+    };
+    // iteration 0 reads the start image; the middle iterations repeat with
+    // period G (in place; thinning epochs of reset_period) and are replayed
+    // from a CUDA graph; the last one (no thinning) writes the caller's buffer
+    int k = 0;
+    rl_status st = issue(k++);
+    if (st != RL_OK) return st;
+    if (!sched && K > 1) {
+        const int G = thin ? thin->reset_period : 10;
+        const int kend = thin ? K : K - 1;
+        int kn = k;
+        st = run_segments(ctx, 1, kend, G >= 2 && G <= 64 ? G : 0, thin ? 1 : 0, issue, args_for, &kn);
+        if (st != RL_OK) return st;
+        ctx->launches += (kn - k) * 2;
+        k = kn;
+    }
+    for (; k < K; ++k) {
+        st = issue(k);
+        if (st != RL_OK) return st;
     }
     if (thin) {
         CK(cudaMemcpy2DAsync(u_out, pitch * es, work, sp * es, W * es, H, cudaMemcpyDeviceToDevice,
@@ -694,47 +775,69 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     }
     const rl::TileShape ts = rl::tile_shape_for(a.ax, a.bx, a.ay, a.by);
     int cur = 0;  // mask plane holding the current mask
-    for (int k = 0; k < K; ++k) {
+    auto args_for = [&](int k) {
+        IterArgs b = a;
         const bool last = k == K - 1;
-        a.u_in = k == 0 ? start : ctx->ubuf[(k - 1) & 1];
-        a.in_pitch = k == 0 ? pitch : sp;
+        b.u_in = k == 0 ? start : ctx->ubuf[(k - 1) & 1];
+        b.in_pitch = k == 0 ? pitch : sp;
         const bool direct = last && !(k == 0 && u_out == start);
-        a.u_out = direct ? u_out : ctx->ubuf[k & 1];
-        a.out_pitch = direct ? pitch : sp;
+        b.u_out = direct ? u_out : ctx->ubuf[k & 1];
+        b.out_pitch = direct ? pitch : sp;
         if (sched) {
-            a.replay = 1;
-            a.full = 0;
-            a.update_mask = 0;
-            a.mask_in = sched + (size_t)k * W * H;
-            a.mi_pitch = W;
-            a.mask_out = ctx->mask[cur];
+            b.replay = 1;
+            b.full = 0;
+            b.update_mask = 0;
+            b.mask_in = sched + (size_t)k * W * H;
+            b.mi_pitch = W;
+            b.mask_out = ctx->mask[cur];
         } else if (thin) {
-            a.full = (k % thin->reset_period) == 0;
-            a.update_mask = thin->update_period == 1 || a.full;
-            a.mask_in = ctx->mask[cur];
-            a.mask_out = ctx->mask[cur ^ 1];
+            b.full = (k % thin->reset_period) == 0;
+            b.update_mask = thin->update_period == 1 || b.full;
+            b.mask_in = ctx->mask[cur];
+            b.mask_out = ctx->mask[cur ^ 1];
         }
+        return b;
+    };
+    auto issue = [&](int k) -> rl_status {
+        const IterArgs b = args_for(k);
         cudaError_t e;
         if (path == RL_PATH_RUNSUM)
-            e = ctx->axis == 0 ? rl::launch_motion_x(a, ctx->storage, thin != nullptr, ctx->stream)
-                               : rl::launch_motion_y(a, ctx->storage, thin != nullptr, ctx->stream);
-        else if (disc_fast)
-            e = rl::launch_disc(a, ctx->storage, thin != nullptr, ctx->disc_radius, ctx->qplane, sp,
-                                ctx->stream);
+            e = ctx->axis == 0 ? rl::launch_motion_x(b, ctx->storage, thin != nullptr, ctx->stream)
+                               : rl::launch_motion_y(b, ctx->storage, thin != nullptr, ctx->stream);
         else
-            e = rl::launch_tile(a, ctx->storage, thin != nullptr,
+            e = rl::launch_tile(b, ctx->storage, thin != nullptr,
                                 path == RL_PATH_SPAN ? rl::TILE_SPAN : rl::TILE_STENCIL, ts, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
-        ctx->launches += disc_fast ? 2 : 1;
-        if (thin && a.update_mask) cur ^= 1;
-        if (thin && !sched) {
-            ctx->last_mask = ctx->mask[cur];
-            ctx->last_W = W;
-            ctx->last_H = H;
-            ctx->last_mp = sp;
-        }
-        if (last && !direct)
-            CK(cudaMemcpy2DAsync(u_out, pitch * es, a.u_out, sp * es, W * es, H,
+        ctx->launches += 1;
+        if (thin && b.update_mask) cur ^= 1;
+        return RL_OK;
+    };
+    int k = 0;
+    rl_status st = issue(k++);
+    if (st != RL_OK) return st;
+    if (!thin && K > 2) {
+        // plain RL: iterations 1 .. K-2 alternate the two scratch buffers,
+        // so a segment of 10 repeats; replay it from a CUDA graph
+        int kn = k;
+        st = run_segments(ctx, 1, K - 1, 10, 2 + path, issue, args_for, &kn);
+        if (st != RL_OK) return st;
+        ctx->launches += kn - k;
+        k = kn;
+    }
+    for (; k < K; ++k) {
+        st = issue(k);
+        if (st != RL_OK) return st;
+    }
+    if (thin && !sched) {
+        ctx->last_mask = ctx->mask[cur];
+        ctx->last_W = W;
+        ctx->last_H = H;
+        ctx->last_mp = sp;
+    }
+    {
+        const IterArgs b = args_for(K - 1);
+        if (b.u_out != u_out)
+            CK(cudaMemcpy2DAsync(u_out, pitch * es, b.u_out, sp * es, W * es, H,
                                  cudaMemcpyDeviceToDevice, ctx->stream),
                "rl_iterate: copy out");
     }
@@ -821,6 +924,19 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
         stats->device_ms = ms;
         stats->path = path;
         stats->launches = ctx->launches;
+        // FP64 flux of the input and the result (diagnostics, after the timing)
+        const int nb = rl::flux_blocks();
+        CK(rl::launch_flux(df, dp, W, H, ctx->storage, ctx->d_flux, ctx->d_flux + nb, ctx->stream),
+           "rl_iterate: flux");
+        CK(rl::launch_flux(staged ? dout : u_out, dp, W, H, ctx->storage, ctx->d_flux,
+                           ctx->d_flux + nb + 1, ctx->stream),
+           "rl_iterate: flux");
+        double fl[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(fl, ctx->d_flux + nb, sizeof fl, cudaMemcpyDeviceToHost, ctx->stream),
+           "rl_iterate: flux");
+        CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: flux");
+        stats->flux_f = fl[0];
+        stats->flux_u = fl[1];
     } else if (staged) {
         CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: sync");
     }

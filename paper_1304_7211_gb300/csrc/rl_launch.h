@@ -24,6 +24,12 @@ cudaError_t launch_motion_x_tb(const IterArgs &a, const TBArgs &tb, int storage,
 size_t motion_x_tb_smem_bytes(int W, int L, bool thin);
 bool motion_x_tb_fits(int W, int L, bool thin);
 
+// FP64 sum of a W x H plane (pitch in elements) of the given storage into
+// *out (device); `partial` holds flux_blocks() doubles.
+int flux_blocks();
+cudaError_t launch_flux(const void *p, long long pitch, int W, int H, int storage, double *partial,
+                        double *out, cudaStream_t s);
+
 // Transpose n_planes planes of W x H elements of `elem_bytes` (4, 2 or 1)
 // from src (pitch sp elements) to dst (H x W, pitch dp elements).
 cudaError_t launch_transpose(const void *src, long long sp, long long s_plane, void *dst,

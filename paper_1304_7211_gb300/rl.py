@@ -61,7 +61,8 @@ class rl_config(ctypes.Structure):
 class rl_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_longlong), ("pixel_iterations", ctypes.c_longlong),
                 ("active_pixel_iterations", ctypes.c_longlong), ("device_ms", ctypes.c_double),
-                ("path", ctypes.c_int), ("launches", ctypes.c_int)]
+                ("path", ctypes.c_int), ("launches", ctypes.c_int),
+                ("flux_f", ctypes.c_double), ("flux_u", ctypes.c_double)]
 
 
 class rl_job(ctypes.Structure):

@@ -392,3 +392,50 @@ def test_resident_rows_thinning(spec, q):
     rep, st, _ = run_flags(spec, f32, 34, 0, thin=th2)
     assert oracle.rel_linf(rep, resq.u) <= TOL
     assert st.active_pixel_iterations == resq.active_pixel_iterations
+
+
+# ---- CUDA-graph replay of iteration segments ------------------------------------
+
+@pytest.mark.parametrize("thin", [None, (2e-3, True, 10, 1), (2e-3, True, 10, 10)])
+@pytest.mark.parametrize("spec", [synth.disc(4), synth.gaussian(7, 1.5), synth.motion(9, 0)],
+                         ids=lambda s: s.name)
+def test_graph_replay_matches_direct_launches(spec, thin):
+    """On an explicit stream the middle iterations are replayed from a captured
+    CUDA graph; on the legacy default stream they are launched one by one.
+    Same kernels, same arguments: identical images, masks and counts."""
+    from paper_1304_7211_gb300 import rl
+    f32 = case(190, 170, spec, seed=synth.SEED_BASE + 54)
+    outs = []
+    for use_stream in (False, True):
+        s = torch.cuda.Stream() if use_stream else None
+        ctx_stream = s.cuda_stream if s is not None else None
+        with torch.cuda.stream(s) if s is not None else torch.cuda.stream(torch.cuda.default_stream()):
+            f = torch.from_numpy(f32).cuda()
+            u = torch.empty_like(f)
+            ctx = rl.rl_create(0, ctx_stream)
+            try:
+                rl.rl_set_psf(ctx, spec)
+                th = rl.thinning(*thin) if thin else None
+                for _ in range(2):  # the second call reuses the cached graph
+                    st = rl.rl_iterate(ctx, f, None, u, 190, 170, 190, 47, th, stats=True)
+                m = np.zeros((170, 190), np.uint8)
+                if thin:
+                    rl.rl_get_mask(ctx, m, 190)
+            finally:
+                rl.rl_destroy(ctx)
+            torch.cuda.synchronize()
+            outs.append((u.cpu().numpy(), m, st.active_pixel_iterations, st.launches))
+    (u0, m0, a0, l0), (u1, m1, a1, l1) = outs
+    np.testing.assert_array_equal(u0, u1)
+    np.testing.assert_array_equal(m0, m1)
+    assert a0 == a1 and l0 == l1
+
+
+def test_flux_diagnostics():
+    from paper_1304_7211_gb300 import rl
+    for spec in (synth.disc(5), synth.motion(13, 1), synth.gaussian(7, 1.5)):
+        f32 = case(230, 170, spec, seed=synth.SEED_BASE + 55)
+        _, st = gpu_rl(spec, f32, 30)
+        ref = float(f32.astype(np.float64).sum())
+        assert abs(st.flux_f - ref) <= 1e-12 * ref
+        assert abs(st.flux_u - st.flux_f) <= 2e-5 * st.flux_f  # flux conservation
