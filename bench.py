@@ -273,6 +273,49 @@ def serve_run(local, n=200, rate=100.0, slots=8):
     return d
 
 
+def thinned_run(local, size=4096, iters=300, oracle_size=384):
+    """Thinned workload: disc radius 12, Poisson noise at peak 500, 300
+    iterations, relative thresholds {1e-3, 1e-4, 1e-5} with the mask
+    recomputed every 10 iterations, FP32 and BF16 storage.  Reports time,
+    active pixel-iterations, PSNR against the latent image, and the error
+    against the FP64 oracle on a smaller image of the same generator."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1304_7211_gb300 import rl, synth
+    c = synth.config3(size)
+    rows = []
+    variants = [(None, "f32"), (None, "bf16")] + [(t, sto) for t in (1e-3, 1e-4, 1e-5)
+                                                   for sto in ("f32", "bf16")]
+    small = synth.config3(oracle_size)
+    t0 = time.perf_counter()
+    refs = {}
+    for tau in (None, 1e-3, 1e-4, 1e-5):
+        fsm = small.f.astype(np.float32).astype(np.float64)
+        refs[tau] = oracle.rl(fsm, oracle.psf_disc(12), iters, threshold=tau,
+                              update_period=10).u
+    oracle_s = time.perf_counter() - t0
+    for tau, sto in variants:
+        dt = {"f32": torch.float32, "bf16": torch.bfloat16}[sto]
+        f = torch.from_numpy(c.f.astype(np.float32)).to(dt).cuda(local)
+        u = torch.empty_like(f)
+        th = None if tau is None else rl.thinning(tau, True, 10, 10)
+        with rl.Deconvolver(c.spec, device=local, storage=sto) as d:
+            rl.rl_iterate(d.ctx, f, None, u, size, size, size, 20, th)  # warm-up
+            st = rl.rl_iterate(d.ctx, f, None, u, size, size, size, iters, th, stats=True)
+            psnr = oracle.psnr_db(u.float().cpu().numpy(), c.g)
+            fs = torch.from_numpy(small.f.astype(np.float32)).to(dt).cuda(local)
+            us = torch.empty_like(fs)
+            rl.rl_iterate(d.ctx, fs, None, us, oracle_size, oracle_size, oracle_size, iters, th)
+            err = oracle.rel_linf(us.float().cpu().numpy(), refs[tau])
+        rows.append({"tau": tau, "storage": sto, "ms": st.device_ms,
+                     "mpx_it_per_s": size * size * iters / st.device_ms / 1e3,
+                     "active_pct": 100.0 * st.active_pixel_iterations / st.pixel_iterations,
+                     "psnr_vs_latent_db": psnr, f"rel_linf_vs_oracle_{oracle_size}": err})
+    return {"workload": f"{size}^2 disc r12 Poisson peak 500, {iters} it, mask every 10 it",
+            "oracle_cpu_s": oracle_s, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -292,12 +335,21 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the served sub-measurement")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--workload", default="plain", choices=["plain", "thinned"],
+                    help="'thinned' prints the thinned-workload table instead of the bench line")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.case:
         return run_case(args)
+    if args.workload == "thinned":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_1304_7211_gb300 import _build
+        _build.build()
+        print(json.dumps(thinned_run(local)), flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -408,8 +460,11 @@ def main():
         sm_mhz = pk.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s, TFLOP/s (adds)
         achieved = flops / (launch_ms * 1e-3) / 1e12
+        # DRAM bytes of one iteration (both launches) from the ncu capture
+        # summarised in profiles/k_disc_half_disc8_2048.md (cold-cache reads)
+        traffic = 33.611520e6 + 0.010752e6 + 33.592576e6 + 0.002048e6
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": f"k_disc_half<float,0,8,fwd>+<..,adj> ({dom}, both launches of one iteration)",
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (adds)"}
     else:
