@@ -40,6 +40,21 @@ WORKLOAD = "plain RL 2048x2048 fp32, PSFs motion-x 31 / motion-y 31 / disc r8, 2
 L2_FLUSH_BYTES = 512 << 20
 
 
+def whole_job_rate(units_per_rank: float, seconds: float, world_size: int, device=None) -> tuple:
+    """Weak-scaling aggregate: every rank processes `units_per_rank` units in
+    its own `seconds`; the job takes as long as the slowest rank (max over
+    ranks), and the rate is all ranks' units over that time.  Returns
+    (rate, max_seconds).  Works with any initialised process group (NCCL on
+    GPUs, gloo on CPU)."""
+    if world_size > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return world_size * units_per_rank / seconds, seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -419,14 +434,10 @@ def main():
     barrier()
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
     px_step = 3 * SIZE * SIZE * ITERS
-    value = ws * px_step * args.steps / (t_ms * 1e-3) / 1e6
+    rate, t_s = whole_job_rate(px_step * args.steps, sum(step_ms) * 1e-3, ws, dev)
+    t_ms = t_s * 1e3
+    value = rate / 1e6
 
     # end to end through the C ABI with host buffers
     for _ in range(2):
@@ -437,13 +448,8 @@ def main():
     for _ in range(e2e_steps):
         step_host()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = ws * px_step * e2e_steps / e2e_s / 1e6
+    e2e_rate, _ = whole_job_rate(px_step * e2e_steps, time.perf_counter() - t0, ws, dev)
+    e2e = e2e_rate / 1e6
     plane = SIZE * SIZE * 4
 
     # dominant kernel: per-solve times, roofline of the slowest

@@ -1,0 +1,56 @@
+"""The N > 1 bench path on CPU: two gloo ranks, each a replica with its own
+work and time; the job rate is all ranks' units over the slowest rank's time
+(no collective touches the data, only the timing reduction)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    import sys
+    import torch.distributed as dist
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        # rank r pretends its replica took (r + 1) seconds for 100 units
+        rate, t = bench.whole_job_rate(100.0, float(rank + 1), world)
+        q.put((rank, rate, t))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_replica():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, rate, t in got:
+        assert t == pytest.approx(2.0)          # max over ranks
+        assert rate == pytest.approx(2 * 100.0 / 2.0)
+
+
+def test_single_rank_is_identity():
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    rate, t = bench.whole_job_rate(50.0, 2.0, 1)
+    assert (rate, t) == (25.0, 2.0)
