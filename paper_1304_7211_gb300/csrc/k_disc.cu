@@ -1,4 +1,4 @@
-// k_disc.cu -- radius dispatch of the disc kernels.
+// k_disc.cu -- radius / size dispatch of the register-blocked disc and stencil kernels.
 #include "rl_launch.h"
 
 namespace rl {
@@ -13,6 +13,17 @@ cudaError_t launch_disc(const IterArgs &a, int storage, bool thin, int radius, f
     RL_DISC_CASE(11) RL_DISC_CASE(12) RL_DISC_CASE(13) RL_DISC_CASE(14) RL_DISC_CASE(15)
     RL_DISC_CASE(16)
 #undef RL_DISC_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil(const IterArgs &a, const float *taps, int K, int storage, bool thin,
+                           float *qplane, long long q_pitch, cudaStream_t s) {
+    switch (K) {
+    case 3: return launch_stencil_k3(a, taps, storage, thin, qplane, q_pitch, s);
+    case 5: return launch_stencil_k5(a, taps, storage, thin, qplane, q_pitch, s);
+    case 7: return launch_stencil_k7(a, taps, storage, thin, qplane, q_pitch, s);
+    case 9: return launch_stencil_k9(a, taps, storage, thin, qplane, q_pitch, s);
     }
     return cudaErrorInvalidValue;
 }

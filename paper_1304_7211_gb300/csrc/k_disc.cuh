@@ -148,6 +148,60 @@ __device__ __forceinline__ void disc_block(const float *src, int pitch, int row0
     }
 }
 
+// Block operations of the generic half-iteration kernel.  kR is the halo
+// radius, kUniform says whether the result still has to be scaled by the
+// uniform tap weight, Params travels in the kernel's parameter block.
+template <int R>
+struct DiscOp {
+    static constexpr int kR = R;
+    static constexpr bool kUniform = true;
+    struct Params {};
+    template <bool FWD>
+    static __device__ __forceinline__ void block(const float *src, int pitch, int row0, int colblk,
+                                                 float (&acc)[SY][SX], const Params &) {
+        disc_block<R>(src, pitch, row0, colblk, acc);  // symmetric: forward = adjoint
+    }
+};
+
+// Dense K x K taps centred on the origin (naive spatial convolution / list
+// filter of Sec. 3 and 5): every tap is a compile-time offset into the
+// register window and a constant-bank operand of its FMA.
+template <int K>
+struct StencilOp {
+    static constexpr int kR = K / 2;
+    static constexpr bool kUniform = false;
+    struct Params { float w[K * K]; };  // w[(ty + R) * K + (tx + R)] = h(tx, ty)
+    template <bool FWD>
+    static __device__ __forceinline__ void block(const float *src, int pitch, int row0, int colblk,
+                                                 float (&acc)[SY][SX], const Params &p) {
+        constexpr int R = K / 2, NW = SX + 2 * R;
+#pragma unroll
+        for (int i = 0; i < SY; ++i)
+#pragma unroll
+            for (int j = 0; j < SX; ++j) acc[i][j] = 0.f;
+        const float *base = src + row0 * pitch + colblk * (SX + 1);
+#pragma unroll
+        for (int m = 0; m < SY + 2 * R; ++m) {
+            float win[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) win[k] = base[m * pitch + k + (k >> 3)];
+#pragma unroll
+            for (int i = 0; i < SY; ++i) {
+                // forward: v(p) = sum_t h(t) u(p - t); adjoint: c(p) = sum_t h(t) q(p + t)
+                const int ty = FWD ? i + R - m : m - i - R;
+                if (ty < -R || ty > R) continue;
+#pragma unroll
+                for (int tx = -R; tx <= R; ++tx) {
+                    const float wv = p.w[(ty + R) * K + (tx + R)];
+#pragma unroll
+                    for (int j = 0; j < SX; ++j)
+                        acc[i][j] = fmaf(wv, win[FWD ? j + R - tx : j + R + tx], acc[i][j]);
+                }
+            }
+        }
+    }
+};
+
 // One half of an RL iteration for a TX x TY output tile (128 threads, one
 // SY x SX block each).  FWD: v = h (x) u and q = f / v on the tile, written
 // to the q plane (inactive pixels keep their q: it is the ratio of their last
@@ -156,8 +210,10 @@ __device__ __forceinline__ void disc_block(const float *src, int pitch, int row0
 // a 2R halo continued across the image border.
 constexpr int TX = 64, TY = 64;
 
-template <typename T, bool THIN, int R, bool FWD>
-__global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane, long long q_pitch) {
+template <typename T, bool THIN, typename Op, bool FWD>
+__global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, const __grid_constant__ typename Op::Params prm,
+                                                      float *qplane, long long q_pitch) {
+    constexpr int R = Op::kR;
     extern __shared__ float sm[];
     constexpr int NSX = TX + 2 * R, NSY = TY + 2 * R;  // staged columns and rows
     constexpr int SP = (NSX + (NSX >> 3)) | 1;         // skewed, odd pitch
@@ -220,7 +276,7 @@ __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane,
         }
         const int xb = x0 + bx * SX, yb = y0 + by * SY;
         float acc[SY][SX];
-        disc_block<R>(sm, SP, by * SY, bx, acc);
+        Op::template block<FWD>(sm, SP, by * SY, bx, acc, prm);
 #pragma unroll
         for (int i = 0; i < SY; ++i) {
             const int y = yb + i;
@@ -234,11 +290,11 @@ __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, float *qplane,
                     if (THIN && !a.full) use = a.mask_in[(long long)y * a.mi_pitch + x] != 0;
                     if (use) {
                         const float fv = Stor<T>::ld((const T *)a.f, (long long)y * a.f_pitch + x);
-                        qplane[(long long)y * q_pitch + x] = rl_ratio(fv, acc[i][j] * a.weight);
+                        qplane[(long long)y * q_pitch + x] = rl_ratio(fv, (Op::kUniform ? acc[i][j] * a.weight : acc[i][j]));
                     }
                 } else {
                     const float u = Stor<T>::ld((const T *)a.u_in, (long long)y * a.in_pitch + x);
-                    const float c = acc[i][j] * a.weight;
+                    const float c = (Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
                     float un = u * c;
                     if (THIN) {
                         const bool use = a.full || a.mask_in[(long long)y * a.mi_pitch + x] != 0;
@@ -279,28 +335,29 @@ constexpr size_t half_smem_bytes() {
     return (size_t)NSY * SP * sizeof(float);
 }
 
-template <int R, typename T, bool THIN>
-cudaError_t launch_one(const IterArgs &a, float *qplane, long long q_pitch, cudaStream_t s) {
-    constexpr size_t smem = half_smem_bytes<R>();
-    cudaError_t e = ensure_smem<k_disc_half<T, THIN, R, true>>(smem);
-    if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, R, false>>(smem);
+template <typename Op, typename T, bool THIN>
+cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float *qplane,
+                       long long q_pitch, cudaStream_t s) {
+    constexpr size_t smem = half_smem_bytes<Op::kR>();
+    cudaError_t e = ensure_smem<k_disc_half<T, THIN, Op, true>>(smem);
+    if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY);
-    k_disc_half<T, THIN, R, true><<<grid, 128, smem, s>>>(a, qplane, q_pitch);
-    k_disc_half<T, THIN, R, false><<<grid, 128, smem, s>>>(a, qplane, q_pitch);
+    k_disc_half<T, THIN, Op, true><<<grid, 128, smem, s>>>(a, prm, qplane, q_pitch);
+    k_disc_half<T, THIN, Op, false><<<grid, 128, smem, s>>>(a, prm, qplane, q_pitch);
     return cudaGetLastError();
 }
 
-template <int R>
-cudaError_t launch_r(const IterArgs &a, int storage, bool thin, float *qplane, long long q_pitch,
-                     cudaStream_t s) {
+template <typename Op>
+cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int storage, bool thin,
+                      float *qplane, long long q_pitch, cudaStream_t s) {
     switch (storage) {
-    case ST_F32: return thin ? launch_one<R, float, true>(a, qplane, q_pitch, s)
-                             : launch_one<R, float, false>(a, qplane, q_pitch, s);
-    case ST_BF16: return thin ? launch_one<R, __nv_bfloat16, true>(a, qplane, q_pitch, s)
-                              : launch_one<R, __nv_bfloat16, false>(a, qplane, q_pitch, s);
-    case ST_F16: return thin ? launch_one<R, __half, true>(a, qplane, q_pitch, s)
-                             : launch_one<R, __half, false>(a, qplane, q_pitch, s);
+    case ST_F32: return thin ? launch_one<Op, float, true>(a, prm, qplane, q_pitch, s)
+                             : launch_one<Op, float, false>(a, prm, qplane, q_pitch, s);
+    case ST_BF16: return thin ? launch_one<Op, __nv_bfloat16, true>(a, prm, qplane, q_pitch, s)
+                              : launch_one<Op, __nv_bfloat16, false>(a, prm, qplane, q_pitch, s);
+    case ST_F16: return thin ? launch_one<Op, __half, true>(a, prm, qplane, q_pitch, s)
+                             : launch_one<Op, __half, false>(a, prm, qplane, q_pitch, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -308,12 +365,23 @@ cudaError_t launch_r(const IterArgs &a, int storage, bool thin, float *qplane, l
 }  // namespace disc
 }  // namespace rl
 
-// One translation unit per radius keeps each compile short and lets them run
-// in parallel.
+// One translation unit per radius / stencil size keeps each compile short and
+// lets them run in parallel.
 #define RL_DISC_RADIUS_TU(R)                                                                 \
     namespace rl {                                                                           \
     cudaError_t launch_disc_r##R(const IterArgs &a, int storage, bool thin, float *qplane,   \
                                  long long q_pitch, cudaStream_t s) {                        \
-        return disc::launch_r<R>(a, storage, thin, qplane, q_pitch, s);                      \
+        return disc::launch_op<disc::DiscOp<R>>(a, {}, storage, thin, qplane, q_pitch, s);  \
+    }                                                                                        \
+    }
+
+#define RL_STENCIL_TU(K)                                                                     \
+    namespace rl {                                                                           \
+    cudaError_t launch_stencil_k##K(const IterArgs &a, const float *taps, int storage,       \
+                                    bool thin, float *qplane, long long q_pitch,             \
+                                    cudaStream_t s) {                                        \
+        disc::StencilOp<K>::Params p;                                                        \
+        for (int i = 0; i < K * K; ++i) p.w[i] = taps[i];                                    \
+        return disc::launch_op<disc::StencilOp<K>>(a, p, storage, thin, qplane, q_pitch, s); \
     }                                                                                        \
     }

@@ -363,6 +363,11 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
     ctx->spans = spans;
     ctx->weight = uniform ? (float)(common / sum) : 0.f;
     ctx->has_psf = true;
+    // a cached graph may carry the old taps in its kernel parameters
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
     ctx->err.clear();
     return RL_OK;
 }
@@ -556,7 +561,8 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
 // updated in place in one working buffer; with thinning, tiles with no active
 // pixel skip both launches.
 rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, int W, int H,
-                   long long pitch, int K, const rl_thinning *thin, long long sp) {
+                   long long pitch, int K, const rl_thinning *thin, long long sp, int stencil_k) {
+    const int R = stencil_k ? stencil_k / 2 : ctx->disc_radius;
     const size_t es = elem_size(ctx->storage);
     const size_t plane = (size_t)sp * H;
     if (ctx->ubuf_bytes < plane * es) {
@@ -575,7 +581,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     a.H = H;
     a.f_pitch = pitch;
     a.clamp = ctx->boundary == RL_BOUNDARY_CLAMP;
-    a.ax = a.bx = a.ay = a.by = ctx->disc_radius;
+    a.ax = a.bx = a.ay = a.by = R;
     a.weight = ctx->weight;
     a.m_pitch = a.mi_pitch = sp;
     const uint8_t *sched = nullptr;
@@ -634,8 +640,10 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     };
     auto issue = [&](int k) -> rl_status {
         const IterArgs b = args_for(k);
-        cudaError_t e = rl::launch_disc(b, ctx->storage, thin != nullptr, ctx->disc_radius, ctx->qplane,
-                                        sp, ctx->stream);
+        cudaError_t e = stencil_k ? rl::launch_stencil(b, ctx->taps.data(), stencil_k, ctx->storage,
+                                                       thin != nullptr, ctx->qplane, sp, ctx->stream)
+                                  : rl::launch_disc(b, ctx->storage, thin != nullptr, ctx->disc_radius,
+                                                    ctx->qplane, sp, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
         ctx->launches += 2;
         return RL_OK;
@@ -650,7 +658,8 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         const int G = thin ? thin->reset_period : 10;
         const int kend = thin ? K : K - 1;
         int kn = k;
-        st = run_segments(ctx, 1, kend, G >= 2 && G <= 64 ? G : 0, thin ? 1 : 0, issue, args_for, &kn);
+        st = run_segments(ctx, 1, kend, G >= 2 && G <= 64 ? G : 0, (thin ? 1 : 0) | stencil_k << 1, issue,
+                          args_for, &kn);
         if (st != RL_OK) return st;
         ctx->launches += (kn - k) * 2;
         k = kn;
@@ -726,7 +735,12 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     }
     const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
                            ctx->disc_radius <= rl::kDiscMaxRadius;
-    if (disc_fast) {
+    // centred odd square taps up to 9 x 9 take the register-blocked stencil
+    const int stencil_k = path == RL_PATH_STENCIL && ctx->kw == ctx->kh && (ctx->kw & 1) && ctx->kw >= 3 &&
+                                  ctx->kw <= 9 && ctx->ax == ctx->kw / 2 && ctx->ay == ctx->kh / 2
+                              ? ctx->kw
+                              : 0;
+    if (disc_fast || stencil_k) {
         if (ctx->q_px < plane) {
             cudaFree(ctx->qplane);
             ctx->qplane = nullptr;
@@ -735,7 +749,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             ctx->q_px = plane;
         }
         if (thin) CK(cudaMemsetAsync(ctx->qplane, 0, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
-        return run_disc(ctx, f, start, u_out, W, H, pitch, K, thin, sp);
+        return run_disc(ctx, f, start, u_out, W, H, pitch, K, thin, sp, stencil_k);
     }
 
     IterArgs a;

@@ -62,4 +62,13 @@ RL_DECLARE_DISC_R(9) RL_DECLARE_DISC_R(10) RL_DECLARE_DISC_R(11) RL_DECLARE_DISC
 RL_DECLARE_DISC_R(13) RL_DECLARE_DISC_R(14) RL_DECLARE_DISC_R(15) RL_DECLARE_DISC_R(16)
 #undef RL_DECLARE_DISC_R
 
+// Register-blocked dense stencil (same two-launch structure as the disc):
+// centred K x K taps, K in {3, 5, 7, 9}; `taps` is a host array of K*K.
+cudaError_t launch_stencil(const IterArgs &a, const float *taps, int K, int storage, bool thin,
+                           float *qplane, long long q_pitch, cudaStream_t s);
+cudaError_t launch_stencil_k3(const IterArgs &, const float *, int, bool, float *, long long, cudaStream_t);
+cudaError_t launch_stencil_k5(const IterArgs &, const float *, int, bool, float *, long long, cudaStream_t);
+cudaError_t launch_stencil_k7(const IterArgs &, const float *, int, bool, float *, long long, cudaStream_t);
+cudaError_t launch_stencil_k9(const IterArgs &, const float *, int, bool, float *, long long, cudaStream_t);
+
 }  // namespace rl

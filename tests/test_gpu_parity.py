@@ -89,6 +89,26 @@ def test_asymmetric_dense_psf_off_centre_anchor():
         assert oracle.rel_linf(u, ref) <= TOL
 
 
+@pytest.mark.parametrize("boundary", ["mirror", "clamp"])
+@pytest.mark.parametrize("k", [3, 5, 7, 9])
+def test_asymmetric_centred_square_taps(k, boundary):
+    # Centred odd square taps take the register-blocked stencil kernel; random
+    # asymmetric taps catch a flipped or transposed tap index in either half.
+    rng = np.random.default_rng(100 + k)
+    taps = rng.uniform(0.05, 1.0, size=(k, k))
+    spec = synth.dense(taps)
+    f32 = case(203, 161, spec, seed=synth.SEED_BASE + 52)
+    u, st = gpu_rl(spec, f32, 30, path="stencil", boundary=boundary)
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 30, boundary=boundary).u
+    assert oracle.rel_linf(u, ref) <= TOL
+    assert st.path == 3
+    # BF16 storage: K x unit roundoff against the oracle on the rounded f
+    f_r = torch.from_numpy(f32).to(torch.bfloat16).float().numpy()
+    u, _ = gpu_rl(spec, f_r, 30, path="stencil", boundary=boundary, storage="bf16")
+    ref = oracle.rl(f_r.astype(np.float64), oracle_psf(spec), 30, boundary=boundary).u
+    assert oracle.rel_linf(u, ref) <= 30 * 2.0 ** -9
+
+
 def test_uniform_rectangle_from_dense_taps_uses_span_path():
     spec = synth.dense(np.ones((3, 5)))
     f32 = case(150, 90, spec)
