@@ -21,6 +21,8 @@
 // inactive pixels are simply not rewritten.
 #pragma once
 
+#include <type_traits>
+
 #include "rl_launch.h"
 
 namespace rl {
@@ -202,6 +204,68 @@ struct StencilOp {
     }
 };
 
+// One thread's row segment of SX = 8 pixels in the epilogue: all loads of
+// the segment are issued before any is used (one memory round trip per row,
+// not per pixel) and go out as 16-byte accesses when the segment is whole
+// and aligned, else as n scalars.
+template <typename T>
+__device__ __forceinline__ void ld_seg(const T *p, int n, float (&v)[SX]) {
+    if (n == SX && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 a = reinterpret_cast<const float4 *>(p)[0];
+            const float4 b = reinterpret_cast<const float4 *>(p)[1];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+            const uint4 r = *reinterpret_cast<const uint4 *>(p);
+            const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned short lo = (unsigned short)(w[k] & 0xffffu), hi = (unsigned short)(w[k] >> 16);
+                if constexpr (std::is_same<T, __half>::value) {
+                    v[2 * k] = __half2float(__ushort_as_half(lo));
+                    v[2 * k + 1] = __half2float(__ushort_as_half(hi));
+                } else {
+                    v[2 * k] = __bfloat162float(__ushort_as_bfloat16(lo));
+                    v[2 * k + 1] = __bfloat162float(__ushort_as_bfloat16(hi));
+                }
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < SX; ++j) v[j] = j < n ? Stor<T>::ld(p, j) : 0.f;
+}
+
+template <typename T>
+__device__ __forceinline__ void st_seg(T *p, int n, const float (&v)[SX]) {
+    if (n == SX && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if constexpr (sizeof(T) == 4) {
+            reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+            unsigned w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                unsigned short lo, hi;
+                if constexpr (std::is_same<T, __half>::value) {
+                    lo = __half_as_ushort(__float2half_rn(v[2 * k]));
+                    hi = __half_as_ushort(__float2half_rn(v[2 * k + 1]));
+                } else {
+                    lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k]));
+                    hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k + 1]));
+                }
+                w[k] = (unsigned)lo | (unsigned)hi << 16;
+            }
+            *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < SX; ++j)
+        if (j < n) Stor<T>::st(p, j, v[j]);
+}
+
 // One half of an RL iteration for a TX x TY output tile (128 threads, one
 // SY x SX block each).  FWD: v = h (x) u and q = f / v on the tile, written
 // to the q plane (inactive pixels keep their q: it is the ratio of their last
@@ -210,8 +274,12 @@ struct StencilOp {
 // a 2R halo continued across the image border.
 constexpr int TX = 64, TY = 64;
 
+// Seven resident CTAs per SM (<= 72 registers) while the staged halo allows it.
+template <int R>
+constexpr int min_blocks() { return R <= 8 ? 7 : 4; }
+
 template <typename T, bool THIN, typename Op, bool FWD>
-__global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, const __grid_constant__ typename Op::Params prm,
+__global__ void __launch_bounds__(128, min_blocks<Op::kR>()) k_disc_half(IterArgs a, const __grid_constant__ typename Op::Params prm,
                                                       float *qplane, long long q_pitch) {
     constexpr int R = Op::kR;
     extern __shared__ float sm[];
@@ -277,6 +345,29 @@ __global__ void __launch_bounds__(128, 4) k_disc_half(IterArgs a, const __grid_c
         const int xb = x0 + bx * SX, yb = y0 + by * SY;
         float acc[SY][SX];
         Op::template block<FWD>(sm, SP, by * SY, bx, acc, prm);
+        if (!THIN) {
+            const int n = min(SX, a.W - xb);
+#pragma unroll
+            for (int i = 0; i < SY; ++i) {
+                const int y = yb + i;
+                if (y >= a.H || n <= 0) break;
+                float e[SX], o[SX];
+                if (FWD) {
+                    ld_seg<T>((const T *)a.f + (long long)y * a.f_pitch + xb, n, e);
+#pragma unroll
+                    for (int j = 0; j < SX; ++j)
+                        o[j] = rl_ratio(e[j], Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
+                    st_seg<float>(qplane + (long long)y * q_pitch + xb, n, o);
+                } else {
+                    ld_seg<T>((const T *)a.u_in + (long long)y * a.in_pitch + xb, n, e);
+#pragma unroll
+                    for (int j = 0; j < SX; ++j)
+                        o[j] = e[j] * (Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
+                    st_seg<T>((T *)a.u_out + (long long)y * a.out_pitch + xb, n, o);
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int i = 0; i < SY; ++i) {
             const int y = yb + i;
