@@ -30,11 +30,17 @@ namespace disc {
 
 constexpr int SX = 8;  // outputs per thread along x
 constexpr int SY = 4;  // outputs per thread along y
+constexpr int TX = 64, TY = 64;  // output tile of one CTA (128 threads)
 
-// Shared-memory column with one skew word every SX columns: a warp's 4 x 8
-// patch of blocks (4 across, 8 down) then reads 32 distinct banks (odd row
-// pitch).
-__device__ __forceinline__ int sk(int c) { return c + (c >> 3); }
+// Shared-memory layout of a staged halo tile: rows of 4-float units, the
+// halo rounded up to R4 = 4 ceil(R / 4) columns on each side so that every
+// unit starts on a 16-byte boundary in the image too.  Unit u of a row is
+// stored at u ^ ((u >> 3) & 1): the 8 lanes of a 16-byte load phase (block
+// columns bx = 0..7 of one block row, reading unit 2 bx + t) then hit 8
+// distinct bank quads for every t.
+__device__ __forceinline__ int hunit(int u) { return u ^ ((u >> 3) & 1); }
+__device__ __forceinline__ int hidx(int c) { return (hunit(c >> 2) << 2) | (c & 3); }
+__host__ __device__ constexpr int round4(int r) { return (r + 3) & ~3; }
 
 // Half-width of the disc's run in PSF row ty: largest s with s^2 + ty^2 <= R^2.
 __host__ __device__ constexpr int run_half_width(int R, int ty) {
@@ -48,60 +54,109 @@ __device__ __forceinline__ void warp_count_add(unsigned long long *ctr, unsigned
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
-// Stage rows [0, nrows) x columns [0, ncols) of an array with skewed columns:
-// element (r, c) is image pixel (y0 + r, x0 + c) when r in [r_lo, r_hi) and
-// c in [c_lo, c_hi) (boundary-mapped unless `inside`), else 0.  One warp per
-// row, four rows in flight.
+__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// Stage the halo tile: array row r, column c (r < nrows, c < 4 nu) is image
+// pixel (y0 + r, xs + c), continued across the border (clamp or mirror).
+// xs is a multiple of 4.  FP32 goes by asynchronous copies -- 16 bytes where
+// the unit lies inside the image and the row is 16-byte aligned, else four
+// 4-byte copies of the boundary-mapped pixels; the caller waits
+// (cp_async_wait_all) before the barrier.  16-bit storage goes through
+// registers, converted to FP32, several units in flight per thread.
 template <typename T>
-__device__ __forceinline__ void stage_rows(float *dst, int pitch, int nrows, int ncols, int r_hi,
-                                           int c_lo, int c_hi, bool inside, int clamp, int W,
-                                           int H, int y0, int x0, const T *src, long long sp,
-                                           int wid, int nwarps, int lane, int r_lo = 0) {
+__device__ __forceinline__ void stage_halo(float *dst, int nrows, int nu, int clamp, int W, int H, int y0,
+                                           int xs, const T *src, long long sp, int tid) {
+    const int total = nrows * nu;
     if constexpr (sizeof(T) == 4) {
-        // FP32: asynchronous global -> shared copies, all of a thread's copies
-        // in flight at once; the caller waits (cp_async_wait_all) before the barrier.
-        for (int r = wid; r < nrows; r += nwarps) {
-            const bool row_in = r >= r_lo && r < r_hi;
-            const int yy = row_in ? (inside ? y0 + r : bmap(y0 + r, H, clamp)) : 0;
-            const float *srow = reinterpret_cast<const float *>(src) + (long long)yy * sp;
-            float *drow = dst + r * pitch;
-            for (int c = lane; c < ncols; c += 32) {
-                if (row_in && c >= c_lo && c < c_hi) {
-                    const int xx = inside ? x0 + c : bmap(x0 + c, W, clamp);
-                    cp_async4(drow + sk(c), srow + xx);
-                } else {
-                    drow[sk(c)] = 0.f;
-                }
+        const float *s = reinterpret_cast<const float *>(src);
+        for (int e = tid; e < total; e += 128) {
+            const int r = e / nu, u = e - r * nu;
+            const int yy = bmap(y0 + r, H, clamp);
+            const float *srow = s + (long long)yy * sp;
+            const int x = xs + 4 * u;
+            float *d = dst + r * 4 * nu + (hunit(u) << 2);
+            if (x >= 0 && x + 4 <= W && (reinterpret_cast<uintptr_t>(srow) & 15) == 0) {
+                cp_async16(d, srow + x);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async4(d + k, srow + bmap(x + k, W, clamp));
             }
         }
         return;
     }
-    // 16-bit storage: loads through registers (converted to FP32), RB rows x
-    // CB column passes in flight per thread.
-    constexpr int RB = 4, CB = 3;
-    for (int rb = wid * RB; rb < nrows; rb += nwarps * RB) {
-        for (int c0 = lane; c0 < ncols; c0 += 32 * CB) {
-            float v[RB][CB];
+    constexpr int B = 4;
+    for (int e0 = tid; e0 < total; e0 += 128 * B) {
+        float v[B][4];
 #pragma unroll
-            for (int k = 0; k < RB; ++k)
+        for (int b = 0; b < B; ++b) {
+            const int e = e0 + 128 * b;
+            if (e < total) {
+                const int r = e / nu, u = e - r * nu;
+                const T *srow = src + (long long)bmap(y0 + r, H, clamp) * sp;
+                const int x = xs + 4 * u;
 #pragma unroll
-                for (int q = 0; q < CB; ++q) {
-                    const int r = rb + k, cb = c0 + 32 * q;
-                    v[k][q] = 0.f;
-                    if (r < nrows && cb < ncols && r >= r_lo && r < r_hi && cb >= c_lo && cb < c_hi) {
-                        int yy = y0 + r, xx = x0 + cb;
-                        if (!inside) {
-                            yy = bmap(yy, H, clamp);
-                            xx = bmap(xx, W, clamp);
-                        }
-                        v[k][q] = Stor<T>::ld(src, (long long)yy * sp + xx);
-                    }
+                for (int k = 0; k < 4; ++k) v[b][k] = Stor<T>::ld(srow, bmap(x + k, W, clamp));
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int e = e0 + 128 * b;
+            if (e < total) {
+                const int r = e / nu, u = e - r * nu;
+                *reinterpret_cast<float4 *>(dst + r * 4 * nu + (hunit(u) << 2)) =
+                    make_float4(v[b][0], v[b][1], v[b][2], v[b][3]);
+            }
+        }
+    }
+}
+
+// Geometry of the staged halo tile for a filter of radius R.
+template <int R>
+struct Halo {
+    static constexpr int R4 = round4(R);           // halo rounded up to whole units
+    static constexpr int NU = (TX + 2 * R4) / 4;   // units per row (even)
+    static constexpr int HP = 4 * NU;              // row pitch in floats
+    static constexpr int NR = TY + 2 * R;          // staged rows
+    static constexpr int NWU = (SX + 2 * R4) / 4;  // units in one block's window
+    static constexpr int OFF = R4 - R;             // window column of offset -R
+    static constexpr size_t bytes = (size_t)NR * HP * sizeof(float);
+};
+
+// The window of block column bx in one staged row: w[k], k < SX + 2R, is the
+// input at offset k - R from the block's first column.  Whole units go as
+// 16-byte loads; the partial units at the two ends load only the columns in
+// use (8- or 4-byte loads: for a warp those take no more shared-memory
+// wavefronts than one 16-byte load, and they keep no dead registers).
+template <int R>
+__device__ __forceinline__ void load_window(const float *row, int bx, float (&w)[SX + 2 * R]) {
+    using G = Halo<R>;
+    constexpr int NW = SX + 2 * R;
+#pragma unroll
+    for (int t = 0; t < G::NWU; ++t) {
+        const float *p = row + (hunit(2 * bx + t) << 2);
+        const int lo = G::OFF - 4 * t > 0 ? G::OFF - 4 * t : 0;
+        const int hi = G::OFF + NW - 4 * t < 4 ? G::OFF + NW - 4 * t : 4;
+        const int d = 4 * t - G::OFF;  // w index of unit column 0
+        if (lo == 0 && hi == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p);
+            w[d] = v.x; w[d + 1] = v.y; w[d + 2] = v.z; w[d + 3] = v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < lo || k >= hi) continue;
+                const bool pair_head = (k & 1) == 0 && k + 1 < hi;
+                const bool pair_tail = (k & 1) == 1 && k - 1 >= lo;
+                if (pair_head) {
+                    const float2 v = *reinterpret_cast<const float2 *>(p + k);
+                    w[d + k] = v.x;
+                    w[d + k + 1] = v.y;
+                } else if (!pair_tail) {
+                    w[d + k] = p[k];
                 }
-#pragma unroll
-            for (int k = 0; k < RB; ++k)
-#pragma unroll
-                for (int q = 0; q < CB; ++q)
-                    if (rb + k < nrows && c0 + 32 * q < ncols) dst[(rb + k) * pitch + sk(c0 + 32 * q)] = v[k][q];
+            }
         }
     }
 }
@@ -110,27 +165,23 @@ __device__ __forceinline__ void stage_rows(float *dst, int pitch, int nrows, int
 // block is array row row0 + m; output row i uses it with ty = i + R - m
 // (forward) -- the adjoint reads the mirrored offset, which has the same run.
 template <int R>
-__device__ __forceinline__ void disc_block(const float *src, int pitch, int row0, int colblk,
-                                           float (&acc)[SY][SX]) {
+__device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&acc)[SY][SX]) {
+    using G = Halo<R>;
     constexpr int NW = SX + 2 * R;
     constexpr int NR = SY + 2 * R;
 #pragma unroll
     for (int i = 0; i < SY; ++i)
 #pragma unroll
         for (int j = 0; j < SX; ++j) acc[i][j] = 0.f;
-    const float *base = src + row0 * pitch + colblk * (SX + 1);
+    const float *base = tile + row0 * G::HP;
     // The window of the next input row is loaded while the current one is
     // summed, so shared-memory latency overlaps the additions.
     float w[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) w[k] = base[k + (k >> 3)];
+    load_window<R>(base, bx, w);
 #pragma unroll
     for (int m = 0; m < NR; ++m) {
         float wn[NW];
-        if (m + 1 < NR) {
-#pragma unroll
-            for (int k = 0; k < NW; ++k) wn[k] = base[(m + 1) * pitch + k + (k >> 3)];
-        }
+        if (m + 1 < NR) load_window<R>(base + (m + 1) * G::HP, bx, wn);
         float P[NW + 1];
         P[0] = 0.f;
 #pragma unroll
@@ -159,9 +210,9 @@ struct DiscOp {
     static constexpr bool kUniform = true;
     struct Params {};
     template <bool FWD>
-    static __device__ __forceinline__ void block(const float *src, int pitch, int row0, int colblk,
-                                                 float (&acc)[SY][SX], const Params &) {
-        disc_block<R>(src, pitch, row0, colblk, acc);  // symmetric: forward = adjoint
+    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
+                                                 const Params &) {
+        disc_block<R>(tile, row0, bx, acc);  // symmetric: forward = adjoint
     }
 };
 
@@ -174,19 +225,23 @@ struct StencilOp {
     static constexpr bool kUniform = false;
     struct Params { float w[K * K]; };  // w[(ty + R) * K + (tx + R)] = h(tx, ty)
     template <bool FWD>
-    static __device__ __forceinline__ void block(const float *src, int pitch, int row0, int colblk,
-                                                 float (&acc)[SY][SX], const Params &p) {
-        constexpr int R = K / 2, NW = SX + 2 * R;
+    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
+                                                 const Params &p) {
+        using G = Halo<K / 2>;
+        constexpr int R = K / 2;
 #pragma unroll
         for (int i = 0; i < SY; ++i)
 #pragma unroll
             for (int j = 0; j < SX; ++j) acc[i][j] = 0.f;
-        const float *base = src + row0 * pitch + colblk * (SX + 1);
+        constexpr int NW = SX + 2 * R, NR = SY + 2 * R;
+        const float *base = tile + row0 * G::HP;
+        // next input row's window loaded while the current one is used
+        float win[NW];
+        load_window<R>(base, bx, win);
 #pragma unroll
-        for (int m = 0; m < SY + 2 * R; ++m) {
-            float win[NW];
-#pragma unroll
-            for (int k = 0; k < NW; ++k) win[k] = base[m * pitch + k + (k >> 3)];
+        for (int m = 0; m < NR; ++m) {
+            float wn[NW];
+            if (m + 1 < NR) load_window<R>(base + (m + 1) * G::HP, bx, wn);
 #pragma unroll
             for (int i = 0; i < SY; ++i) {
                 // forward: v(p) = sum_t h(t) u(p - t); adjoint: c(p) = sum_t h(t) q(p + t)
@@ -199,6 +254,10 @@ struct StencilOp {
                     for (int j = 0; j < SX; ++j)
                         acc[i][j] = fmaf(wv, win[FWD ? j + R - tx : j + R + tx], acc[i][j]);
                 }
+            }
+            if (m + 1 < NR) {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) win[k] = wn[k];
             }
         }
     }
@@ -272,19 +331,18 @@ __device__ __forceinline__ void st_seg(T *p, int n, const float (&v)[SX]) {
 // active iteration, Eq. 5).  !FWD: c = h* (x) q and u' = u c with the
 // selective-convolution bookkeeping.  The input plane (u or q) is staged with
 // a 2R halo continued across the image border.
-constexpr int TX = 64, TY = 64;
 
-// Seven resident CTAs per SM (<= 72 registers) while the staged halo allows it.
-template <int R>
-constexpr int min_blocks() { return R <= 8 ? 7 : 4; }
+// Seven resident CTAs per SM (<= 72 registers) while the staged halo allows
+// it; the selective-convolution variant needs more registers.
+template <int R, bool THIN>
+constexpr int min_blocks() { return R > 8 ? 4 : THIN || R == 1 ? 5 : 7; }
 
 template <typename T, bool THIN, typename Op, bool FWD>
-__global__ void __launch_bounds__(128, min_blocks<Op::kR>()) k_disc_half(IterArgs a, const __grid_constant__ typename Op::Params prm,
+__global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(IterArgs a, const __grid_constant__ typename Op::Params prm,
                                                       float *qplane, long long q_pitch) {
     constexpr int R = Op::kR;
+    using G = Halo<R>;
     extern __shared__ float sm[];
-    constexpr int NSX = TX + 2 * R, NSY = TY + 2 * R;  // staged columns and rows
-    constexpr int SP = (NSX + (NSX >> 3)) | 1;         // skewed, odd pitch
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
@@ -292,21 +350,18 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR>()) k_disc_half(IterArg
     // is active does nothing (u stays, q keeps the stale ratios).
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + blockIdx.y * a.tiles_x + blockIdx.x : nullptr;
     if (tflag && !a.full && *tflag == 0) return;
-    {
-        const bool inside = x0 - R >= 0 && x0 + TX + R <= a.W && y0 - R >= 0 && y0 + TY + R <= a.H;
-        if (FWD)
-            stage_rows<T>(sm, SP, NSY, NSX, NSY, 0, NSX, inside, a.clamp, a.W, a.H, y0 - R, x0 - R,
-                          (const T *)a.u_in, a.in_pitch, wid, 4, lane);
-        else
-            stage_rows<float>(sm, SP, NSY, NSX, NSY, 0, NSX, inside, a.clamp, a.W, a.H, y0 - R,
-                              x0 - R, qplane, q_pitch, wid, 4, lane);
-        cp_async_wait_all();
-    }
+    if (FWD)
+        stage_halo<T>(sm, G::NR, G::NU, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
+                      threadIdx.x);
+    else
+        stage_halo<float>(sm, G::NR, G::NU, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
+                          threadIdx.x);
+    cp_async_wait_all();
     __syncthreads();
-    // warp w covers the 32 x 32 quarter (w & 1, w >> 1); lane = 4 (x) x 8 (y) blocks
-    // Natural block of this thread: warp w covers the 32 x 32 quarter
-    // (w & 1, w >> 1); lane = 4 (x) x 8 (y) blocks.
-    const int nbx = (wid & 1) * 4 + (lane & 3), nby = (wid >> 1) * 8 + (lane >> 2);
+    // Natural block of this thread: warp w covers block rows 4w .. 4w + 3,
+    // lane = 8 (x) x 4 (y) blocks, so the 8 lanes of a 16-byte load phase
+    // share a block row.
+    const int nbx = lane & 7, nby = wid * 4 + (lane >> 3);
     // Selective convolution: compact the blocks with at least one pixel used
     // this iteration (warp ballot + prefix over the warps) and convolve only
     // those; warps left without blocks retire early.
@@ -335,6 +390,7 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR>()) k_disc_half(IterArg
         if (any) blist[off + __popc(bal & ((1u << lane) - 1u))] = nby * (TX / SX) + nbx;
         __syncthreads();
     }
+#pragma unroll 1
     for (int e = threadIdx.x; e < n_active; e += 128) {
         int bx = nbx, by = nby;
         if (THIN && !a.full) {
@@ -344,7 +400,7 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR>()) k_disc_half(IterArg
         }
         const int xb = x0 + bx * SX, yb = y0 + by * SY;
         float acc[SY][SX];
-        Op::template block<FWD>(sm, SP, by * SY, bx, acc, prm);
+        Op::template block<FWD>(sm, by * SY, bx, acc, prm);
         if (!THIN) {
             const int n = min(SX, a.W - xb);
 #pragma unroll
@@ -419,17 +475,10 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR>()) k_disc_half(IterArg
     }
 }
 
-template <int R>
-constexpr size_t half_smem_bytes() {
-    constexpr int NSX = TX + 2 * R, NSY = TY + 2 * R;
-    constexpr int SP = (NSX + (NSX >> 3)) | 1;
-    return (size_t)NSY * SP * sizeof(float);
-}
-
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                        long long q_pitch, cudaStream_t s) {
-    constexpr size_t smem = half_smem_bytes<Op::kR>();
+    constexpr size_t smem = Halo<Op::kR>::bytes;
     cudaError_t e = ensure_smem<k_disc_half<T, THIN, Op, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
