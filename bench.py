@@ -195,12 +195,15 @@ def run_case(args):
     with rl.Deconvolver(spec, path=args.path, storage=args.storage) as d:
         rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th)
         torch.cuda.synchronize()
-        st = rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th,
-                           stats=True)
+        runs = [rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th,
+                              stats=True) for _ in range(max(1, args.repeat))]
+    ms = sorted(r.device_ms for r in runs)
+    med = ms[len(ms) // 2]
+    st = runs[-1]
     act = st.active_pixel_iterations / max(st.pixel_iterations, 1)
     print(f"case {spec.name} {args.size}^2 x {args.iters} it {args.storage} tau={args.tau}: "
-          f"{st.device_ms:.3f} ms ({st.device_ms / args.iters * 1e3:.1f} us/it) "
-          f"path={rl.PATH_NAME[st.path]} active={100 * act:.1f}% launches={st.launches}")
+          f"{med:.3f} ms ({med / args.iters * 1e3:.1f} us/it; min {ms[0] / args.iters * 1e3:.1f}, "
+          f"{len(ms)} runs) path={rl.PATH_NAME[st.path]} active={100 * act:.1f}% launches={st.launches}")
     return 0
 
 
@@ -341,6 +344,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="profiling mode: run one solve of this PSF (e.g. disc8, motionx31, "
                          "motiony31, dense7x7) and print its time; no JSON line")
+    ap.add_argument("--repeat", type=int, default=1, help="case mode: timed solves (median reported)")
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--path", default="auto")

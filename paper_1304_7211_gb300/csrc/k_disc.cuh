@@ -66,10 +66,10 @@ __device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_sr
 // 4-byte copies of the boundary-mapped pixels; the caller waits
 // (cp_async_wait_all) before the barrier.  16-bit storage goes through
 // registers, converted to FP32, several units in flight per thread.
-template <typename T>
-__device__ __forceinline__ void stage_halo(float *dst, int nrows, int nu, int clamp, int W, int H, int y0,
-                                           int xs, const T *src, long long sp, int tid) {
-    const int total = nrows * nu;
+template <typename T, int nrows, int nu>
+__device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, int y0, int xs, const T *src,
+                                           long long sp, int tid) {
+    constexpr int total = nrows * nu;
     if constexpr (sizeof(T) == 4) {
         const float *s = reinterpret_cast<const float *>(src);
         for (int e = tid; e < total; e += 128) {
@@ -164,15 +164,32 @@ __device__ __forceinline__ void load_window(const float *row, int bx, float (&w)
 // Sum of the disc over the block's SY x SX outputs.  Input row m of the
 // block is array row row0 + m; output row i uses it with ty = i + R - m
 // (forward) -- the adjoint reads the mirrored offset, which has the same run.
+// Packed pairs of FP32 values (one 64-bit register pair) and the paired add
+// of sm_100+ (add.rn.f32x2: two IEEE round-to-nearest adds in one
+// instruction, each bitwise equal to the scalar add).
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void f2add(unsigned long long &acc, unsigned long long d) {
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(d));
+}
+
 template <int R>
-__device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&acc)[SY][SX]) {
+__device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&out)[SY][SX]) {
     using G = Halo<R>;
     constexpr int NW = SX + 2 * R;
     constexpr int NR = SY + 2 * R;
+    // accumulators of output columns (2h, 2h + 1) as packed pairs
+    unsigned long long acc[SY][SX / 2];
 #pragma unroll
     for (int i = 0; i < SY; ++i)
 #pragma unroll
-        for (int j = 0; j < SX; ++j) acc[i][j] = 0.f;
+        for (int h = 0; h < SX / 2; ++h) acc[i][h] = 0ull;
     const float *base = tile + row0 * G::HP;
     // The window of the next input row is loaded while the current one is
     // summed, so shared-memory latency overlaps the additions.
@@ -192,13 +209,20 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
             if (ty < -R || ty > R) continue;
             const int s = run_half_width(R, ty);
 #pragma unroll
-            for (int j = 0; j < SX; ++j) acc[i][j] += P[j + R + 1 + s] - P[j + R - s];
+            for (int h = 0; h < SX / 2; ++h) {
+                const int j = 2 * h;
+                f2add(acc[i][h], f2pack(P[j + R + 1 + s] - P[j + R - s], P[j + R + 2 + s] - P[j + 1 + R - s]));
+            }
         }
         if (m + 1 < NR) {
 #pragma unroll
             for (int k = 0; k < NW; ++k) w[k] = wn[k];
         }
     }
+#pragma unroll
+    for (int i = 0; i < SY; ++i)
+#pragma unroll
+        for (int h = 0; h < SX / 2; ++h) f2unpack(acc[i][h], out[i][2 * h], out[i][2 * h + 1]);
 }
 
 // Block operations of the generic half-iteration kernel.  kR is the halo
@@ -351,11 +375,11 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + blockIdx.y * a.tiles_x + blockIdx.x : nullptr;
     if (tflag && !a.full && *tflag == 0) return;
     if (FWD)
-        stage_halo<T>(sm, G::NR, G::NU, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
-                      threadIdx.x);
+        stage_halo<T, G::NR, G::NU>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
+                                    threadIdx.x);
     else
-        stage_halo<float>(sm, G::NR, G::NU, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
-                          threadIdx.x);
+        stage_halo<float, G::NR, G::NU>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
+                                        threadIdx.x);
     cp_async_wait_all();
     __syncthreads();
     // Natural block of this thread: warp w covers block rows 4w .. 4w + 3,
