@@ -33,7 +33,11 @@
  *     larger image arrives, and is freed by rl_destroy.
  *   - Work is issued on the context's CUDA stream (rl_config.stream; NULL =
  *     the legacy default stream).  Calls return when the work is queued,
- *     except where stated.
+ *     except where stated.  For a context on the legacy or per-thread default
+ *     stream, rl_iterate runs its kernels on an internal non-blocking stream
+ *     (so that its iteration loop can be replayed as a CUDA graph), ordered
+ *     after the work already queued on the default stream, and the default
+ *     stream waits for it: the ordering seen by the caller is unchanged.
  */
 #ifndef RL_GB300_H
 #define RL_GB300_H

@@ -367,6 +367,12 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
     constexpr int R = Op::kR;
     using G = Halo<R>;
     extern __shared__ float sm[];
+    // Programmatic dependent launch: this grid may start while the previous
+    // kernel of the stream drains; every read of its output (u, q, the tile
+    // flags) comes after this wait, and the next grid may launch as soon as
+    // every CTA of this one has started.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
@@ -506,10 +512,19 @@ cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float 
     cudaError_t e = ensure_smem<k_disc_half<T, THIN, Op, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY);
-    k_disc_half<T, THIN, Op, true><<<grid, 128, smem, s>>>(a, prm, qplane, q_pitch);
-    k_disc_half<T, THIN, Op, false><<<grid, 128, smem, s>>>(a, prm, qplane, q_pitch);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.W + TX - 1) / TX, (a.H + TY - 1) / TY);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_disc_half<T, THIN, Op, true>, a, prm, qplane, q_pitch);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_disc_half<T, THIN, Op, false>, a, prm, qplane, q_pitch);
+    return e;
 }
 
 template <typename Op>

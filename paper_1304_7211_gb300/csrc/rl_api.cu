@@ -44,6 +44,11 @@ struct rl_ctx {
     char *h_psf = nullptr;        // pinned staging of taps + spans
     size_t h_psf_cap = 0;
     cudaEvent_t ev_psf = nullptr; // last PSF upload
+    // The legacy / per-thread default stream cannot be captured into a CUDA
+    // graph: for a context created on it, rl_iterate runs on this internal
+    // non-blocking stream, fenced by events to the caller's stream.
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     double *d_flux = nullptr;     // flux_blocks() partials + 2 results
     // cached CUDA graph of one segment of iterations (see run_segments)
     cudaGraphExec_t gexec = nullptr;
@@ -181,6 +186,12 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_psf, cudaEventDisableTiming);
+    if (e == cudaSuccess && (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy ||
+                             ctx->stream == cudaStreamPerThread)) {
+        e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+    }
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         g_create_error = std::string("rl_create: ") + cudaGetErrorString(e);
@@ -221,6 +232,12 @@ rl_status rl_destroy(rl_ctx *ctx) {
     if (ctx->h_psf) cudaFreeHost(ctx->h_psf);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own) {
+        cudaStreamSynchronize(ctx->own);
+        cudaStreamDestroy(ctx->own);
+    }
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     cudaSetDevice(prev);
     delete ctx;
     return RL_OK;
@@ -887,6 +904,25 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
         int d, p;
         ~Restore() { if (d != p) cudaSetDevice(p); }
     } restore{ctx->device, prev};
+    // Default-stream contexts: the call's work goes to the internal stream,
+    // after everything already queued on the caller's stream, and the
+    // caller's stream waits for it on every return path.
+    struct Fence {
+        rl_ctx *c;
+        cudaStream_t user;
+        ~Fence() {
+            if (!c) return;
+            cudaEventRecord(c->ev_out, c->own);
+            cudaStreamWaitEvent(user, c->ev_out, 0);
+            c->stream = user;
+        }
+    } fence{nullptr, ctx->stream};
+    if (ctx->own) {
+        CK(cudaEventRecord(ctx->ev_in, ctx->stream), "rl_iterate: stream fence");
+        CK(cudaStreamWaitEvent(ctx->own, ctx->ev_in, 0), "rl_iterate: stream fence");
+        ctx->stream = ctx->own;
+        fence.c = ctx;
+    }
 
     const bool dev_f = is_device_ptr(f), dev_o = is_device_ptr(u_out);
     const bool dev_u = u0 ? is_device_ptr(u0) : true;
