@@ -472,10 +472,10 @@ def main():
         achieved = flops / (launch_ms * 1e-3) / 1e12
         # DRAM bytes of one iteration (both launches) from the ncu capture
         # summarised in profiles/k_disc_half_disc8_2048.md (cold-cache reads)
-        traffic = 33.611520e6 + 0.010752e6 + 33.592576e6 + 0.002048e6
+        traffic = 33.597952e6 + 0.001536e6 + 33.586944e6 + 0.0
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"k_disc_half<float,0,8,fwd>+<..,adj> ({dom}, both launches of one iteration)",
+                "kernel": f"k_disc_half<float,0,DiscOp<8>,FWD>+<..,ADJ> ({dom}, both launches of one iteration)",
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (adds)"}
     else:
         bytes_ = px * 12
