@@ -132,6 +132,17 @@ typedef struct {
 #define RL_FLAG_PER_ITERATION 1 /* one launch per iteration even where the
                                    running-sum path could keep whole rows
                                    resident for all iterations            */
+/* The adjoint convolution of Eq. 3.  Default: h* (x) q with the same
+ * boundary continuation as the forward one -- h reflected about the origin
+ * (Sec. 2), the "pad-flip" operator B.  With this flag: the exact matrix
+ * transpose A^T of the forward operator A (u -> h (x) u with the boundary
+ * continuation), i.e. the zero-padded correlation of q folded back onto the
+ * pixels the boundary map sends each padded position to.  The two are the
+ * same operator for a PSF symmetric in each axis under the mirror boundary
+ * (those keep their fast paths); otherwise (clamp, off-centre or asymmetric
+ * taps) A^T makes RL conserve flux exactly and the solve runs on the
+ * generic stencil path. */
+#define RL_FLAG_ADJOINT_TRANSPOSE 2
 
 typedef struct {
     int device;     /* CUDA device ordinal                                   */

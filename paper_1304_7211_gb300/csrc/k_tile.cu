@@ -47,12 +47,43 @@ __device__ __forceinline__ void p_range(int lo, int hi, int n, int clamp, int &p
     p1 = min(n, b);
 }
 
+// Exact-transpose adjoint (A^T): the q region is the adjoint's reach
+// [lo - a_, hi + b_) plus, for outputs that receive folded contributions, the
+// image pixels those contributions read: [0, b_) at the low end and
+// [n - a_, n) at the high end.  P is its part inside the image; q is zero
+// outside the image.
+__device__ __forceinline__ void t_range(int lo, int hi, int n, int ext_lo, int ext_hi, int clamp, int &q0,
+                                        int &q1) {
+    q0 = lo - ext_lo;
+    q1 = hi + ext_hi;
+    if (lo < (clamp ? 1 : ext_hi)) q0 = min(q0, 0);      // outputs with a low-end fold
+    if (hi > (clamp ? n - 1 : n - ext_lo)) q1 = max(q1, n);  // outputs with a high-end fold
+}
+
 __device__ __forceinline__ Geo make_geo(const IterArgs &a, int TX, int TY) {
     Geo g;
     g.x0 = blockIdx.x * TX;
     g.y0 = blockIdx.y * TY;
     g.x1 = min(g.x0 + TX, a.W);
     g.y1 = min(g.y0 + TY, a.H);
+    if (a.transpose) {
+        int qx1, qy1;
+        t_range(g.x0, g.x1, a.W, a.ax, a.bx, a.clamp, g.qx0, qx1);
+        t_range(g.y0, g.y1, a.H, a.ay, a.by, a.clamp, g.qy0, qy1);
+        g.px0 = max(0, g.qx0);
+        g.px1 = min(a.W, qx1);
+        g.py0 = max(0, g.qy0);
+        g.py1 = min(a.H, qy1);
+        g.QW = qx1 - g.qx0;
+        g.QH = qy1 - g.qy0;
+        g.QP = g.QW | 1;
+        g.ux0 = g.px0 - a.bx;
+        g.uy0 = g.py0 - a.by;
+        g.UW = g.px1 - g.px0 + a.ax + a.bx;
+        g.UH = g.py1 - g.py0 + a.ay + a.by;
+        g.UP = g.UW | 1;
+        return g;
+    }
     // q region read by the adjoint: [x0 - ax, x1 + bx) x [y0 - ay, y1 + by);
     // the array also covers P, which can reach past it for off-centre anchors.
     p_range(g.x0 - a.ax, g.x1 + a.bx, a.W, a.clamp, g.px0, g.px1);
@@ -157,6 +188,61 @@ __device__ __forceinline__ void adj_chunk(const IterArgs &a, const Geo &g, const
     }
 }
 
+// Exact-transpose adjoint at image pixel s: (A^T q)(s) is the sum, over the
+// padded positions e with m(e) = s, of z(e) = sum_t h(t) q0(e + t) (q0 = q in
+// the image, 0 outside).  adj_chunk on the zero-filled q tile gives the
+// e = s term; fold_sum adds the others.  Along one axis of length n, z(e)
+// can be non-zero only for e in [-b_, n - 1 + a_]; the positions other than
+// s that map to s there are, for the mirror, -1 - s and 2n - 1 - s, and for
+// clamp, [-b_, -1] (s = 0) and [n, n - 1 + a_] (s = n - 1).
+__device__ __forceinline__ int fold_ranges(int s, int n, int ext_lo, int ext_hi, int clamp, int (&r)[2][2]) {
+    int k = 0;
+    if (clamp) {
+        if (s == 0 && ext_hi >= 1) { r[k][0] = -ext_hi; r[k][1] = -1; ++k; }
+        if (s == n - 1 && ext_lo >= 1) { r[k][0] = n; r[k][1] = n - 1 + ext_lo; ++k; }
+    } else {
+        if (-1 - s >= -ext_hi) { r[k][0] = r[k][1] = -1 - s; ++k; }
+        if (2 * n - 1 - s <= n - 1 + ext_lo) { r[k][0] = r[k][1] = 2 * n - 1 - s; ++k; }
+    }
+    return k;
+}
+
+__device__ __forceinline__ float zval(const IterArgs &a, const Geo &g, const float *Q, const float *taps, int ex,
+                                      int ey) {
+    const int kw = a.ax + a.bx + 1;
+    float z = 0.f;
+    for (int jr = 0; jr <= a.ay + a.by; ++jr) {
+        const int y = ey + jr - a.ay;
+        if (y < 0 || y >= a.H) continue;
+        const float *row = Q + (y - g.qy0) * g.QP - g.qx0;
+        for (int i = 0; i < kw; ++i) {
+            const int x = ex + i - a.ax;
+            const float wt = taps[jr * kw + i];
+            if (x >= 0 && x < a.W && wt != 0.f) z = fmaf(wt, row[x], z);
+        }
+    }
+    return z;
+}
+
+__device__ float fold_sum(const IterArgs &a, const Geo &g, const float *Q, const float *taps, int sx, int sy) {
+    int rx[2][2], ry[2][2];
+    // x positions of z: [-bx, W - 1 + ax]; y: [-by, H - 1 + ay]
+    const int nx = fold_ranges(sx, a.W, a.ax, a.bx, a.clamp, rx);
+    const int ny = fold_ranges(sy, a.H, a.ay, a.by, a.clamp, ry);
+    if (nx == 0 && ny == 0) return 0.f;
+    float acc = 0.f;
+    for (int ix = -1; ix < nx; ++ix) {
+        const int xlo = ix < 0 ? sx : rx[ix][0], xhi = ix < 0 ? sx : rx[ix][1];
+        for (int iy = -1; iy < ny; ++iy) {
+            if (ix < 0 && iy < 0) continue;  // e = s: the main term
+            const int ylo = iy < 0 ? sy : ry[iy][0], yhi = iy < 0 ? sy : ry[iy][1];
+            for (int ex = xlo; ex <= xhi; ++ex)
+                for (int ey = ylo; ey <= yhi; ++ey) acc += zval(a, g, Q, taps, ex, ey);
+        }
+    }
+    return acc;
+}
+
 template <typename T, bool THIN, int MODE>
 __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf_floats) {
     extern __shared__ float sm[];
@@ -227,14 +313,19 @@ __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf
         }
     }
     __syncthreads();
-    // continue q beyond the image borders
+    // continue q beyond the image borders (pad-flip adjoint), or zero it there
+    // (exact transpose: the folded contributions are added per output below)
     if (g.qx0 < 0 || g.qy0 < 0 || g.qx0 + g.QW > a.W || g.qy0 + g.QH > a.H) {
         for (int i = threadIdx.x; i < g.QH * g.QW; i += NT) {
             const int r = i / g.QW, c = i - r * g.QW;
             const int ey = g.qy0 + r, ex = g.qx0 + c;
             if (ey < 0 || ey >= a.H || ex < 0 || ex >= a.W) {
-                const int sy = bmap(ey, a.H, a.clamp), sx = bmap(ex, a.W, a.clamp);
-                Q[r * g.QP + c] = Q[(sy - g.qy0) * g.QP + (sx - g.qx0)];
+                if (a.transpose) {
+                    Q[r * g.QP + c] = 0.f;
+                } else {
+                    const int sy = bmap(ey, a.H, a.clamp), sx = bmap(ex, a.W, a.clamp);
+                    Q[r * g.QP + c] = Q[(sy - g.qy0) * g.QP + (sx - g.qx0)];
+                }
             }
         }
         __syncthreads();
@@ -249,6 +340,16 @@ __global__ void __launch_bounds__(NT) k_tile(IterArgs a, int TX, int TY, int psf
             const int n = min(CHX, g.x1 - px);
             float c[CHX];
             adj_chunk<MODE>(a, g, Q, spans, taps, px, py, n, c);
+            if (MODE == TILE_STENCIL && a.transpose) {
+                // outputs near the border receive the folded contributions
+                const bool ybord = py < a.by || py >= a.H - a.ay || (a.clamp && (py == 0 || py == a.H - 1));
+                const bool xbord = px < a.bx || px + n > a.W - a.ax || (a.clamp && (px == 0 || px + n == a.W));
+                if (ybord || xbord) {
+#pragma unroll
+                    for (int j = 0; j < CHX; ++j)
+                        if (j < n) c[j] += fold_sum(a, g, Q, taps, px + j, py);
+                }
+            }
             float *urow = U + (py - g.uy0) * g.UP + (px - g.ux0);
             const float *qrow = Q + (py - g.qy0) * g.QP + (px - g.qx0);
 #pragma unroll
@@ -289,8 +390,12 @@ size_t tile_smem_bytes(const IterArgs &a, TileShape ts, int mode, int *psf_float
     pf = (pf + 3) & ~3;
     const int ex = a.ax + a.bx, ey = a.ay + a.by;
     // P spans at most tile + ex per axis, so u needs tile + 2 ex; the q array
-    // (q region united with P) is bounded by tile + 2 ex as well.
-    const int UW = ts.tx + 2 * ex, UH = ts.ty + 2 * ey;
+    // (q region united with P) is bounded by tile + 2 ex as well.  With the
+    // exact transpose, P is the q region inside the image, which can reach
+    // tile + 2 max(a_, b_) where fold sources widen it: u then needs up to
+    // tile + 3 ex.
+    const int uf = a.transpose ? 3 : 2;
+    const int UW = ts.tx + uf * ex, UH = ts.ty + uf * ey;
     const int QW = ts.tx + 2 * ex, QH = ts.ty + 2 * ey;
     *psf_floats = pf;
     return (size_t)(pf + UH * (UW | 1) + QH * (QW | 1)) * sizeof(float);

@@ -36,6 +36,7 @@ struct rl_ctx {
     int kw = 0, kh = 0, ax = 0, ay = 0;  // dense layout; bx = kw-1-ax, by = kh-1-ay
     std::vector<float> taps;             // normalised, row-major kh x kw
     bool uniform = false;                // one contiguous run of equal taps per row
+    bool axis_sym = false;               // h(tx, ty) = h(-tx, ty) = h(tx, -ty)
     std::vector<int2> spans;             // per row j: [lo, hi] offsets (lo > hi = empty)
     float weight = 0.f;                  // the common tap value when uniform
     float *d_taps = nullptr;
@@ -320,6 +321,14 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
 
     std::vector<float> tf(t.size());
     for (size_t k = 0; k < t.size(); ++k) tf[k] = (float)(t[k] / sum);
+    // Symmetric in each axis about the anchor: then the pad-flip adjoint under
+    // the mirror boundary is the exact transpose.
+    bool axis_sym = ax == kw - 1 - ax && ay == kh - 1 - ay;
+    for (int j = 0; j < kh && axis_sym; ++j)
+        for (int i = 0; i < kw && axis_sym; ++i) {
+            const double v = t[(size_t)j * kw + i];
+            axis_sym = v == t[(size_t)j * kw + (kw - 1 - i)] && v == t[(size_t)(kh - 1 - j) * kw + i];
+        }
 
     // Stream-ordered upload through a pinned staging buffer; device buffers
     // only grow, so changing the PSF between calls neither allocates nor
@@ -377,6 +386,7 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
     ctx->ay = ay;
     ctx->taps = tf;
     ctx->uniform = uniform;
+    ctx->axis_sym = axis_sym;
     ctx->spans = spans;
     ctx->weight = uniform ? (float)(common / sum) : 0.f;
     ctx->has_psf = true;
@@ -393,8 +403,16 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
 
 namespace {
 
+// Exact-transpose adjoint requested where it differs from the pad-flip one.
+bool needs_fold(const rl_ctx *ctx) {
+    return (ctx->flags & RL_FLAG_ADJOINT_TRANSPOSE) &&
+           !(ctx->boundary == RL_BOUNDARY_MIRROR && ctx->axis_sym);
+}
+
 int choose_path(const rl_ctx *ctx, int W) {
     const int L = ctx->kind == RL_PSF_MOTION ? (ctx->axis == 0 ? ctx->kw : ctx->kh) : 0;
+    // the folded transpose is computed by the generic stencil tiles
+    if (needs_fold(ctx)) return RL_PATH_STENCIL;
     int p = ctx->path_pref;
     if (p == RL_PATH_AUTO) {
         if (ctx->kind == RL_PSF_MOTION) p = RL_PATH_RUNSUM;
@@ -753,7 +771,8 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
                            ctx->disc_radius <= rl::kDiscMaxRadius;
     // centred odd square taps up to 9 x 9 take the register-blocked stencil
-    const int stencil_k = path == RL_PATH_STENCIL && ctx->kw == ctx->kh && (ctx->kw & 1) && ctx->kw >= 3 &&
+    const int stencil_k = path == RL_PATH_STENCIL && !needs_fold(ctx) && ctx->kw == ctx->kh && (ctx->kw & 1) &&
+                                  ctx->kw >= 3 &&
                                   ctx->kw <= 9 && ctx->ax == ctx->kw / 2 && ctx->ay == ctx->kh / 2
                               ? ctx->kw
                               : 0;
@@ -786,6 +805,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     a.m_pitch = sp;
     a.mi_pitch = sp;
     a.rstale = ctx->rstale;
+    a.transpose = needs_fold(ctx);
     const uint8_t *sched = nullptr;
     if (thin && thin->schedule) {
         const size_t bytes = (size_t)W * H * K;

@@ -211,6 +211,7 @@ struct IterArgs {
     unsigned long long *active_count;        // += used pixels (nullable)
     int *tile_flags;                         // per tile: any pixel active next (nullable)
     int tiles_x;                             // tiles per row of tile_flags
+    int transpose;                           // adjoint = exact transpose A^T (STENCIL tiles)
 };
 
 // Several iterations in one launch (kernels that keep their lines resident).

@@ -50,6 +50,8 @@ class rl_thinning(ctypes.Structure):
 
 
 RL_FLAG_PER_ITERATION = 1
+RL_FLAG_ADJOINT_TRANSPOSE = 2
+ADJOINT = {"padflip": 0, "transpose": RL_FLAG_ADJOINT_TRANSPOSE}
 
 
 class rl_config(ctypes.Structure):
@@ -252,8 +254,9 @@ class Deconvolver:
     """
 
     def __init__(self, spec, device: int = 0, storage="f32", boundary="mirror",
-                 path="auto", stream=None, flags: int = 0):
+                 path="auto", stream=None, flags: int = 0, adjoint="padflip"):
         self.device = device
+        flags |= ADJOINT[adjoint]
         self.storage = storage
         if stream is None:
             try:
