@@ -184,7 +184,9 @@ def run_case(args):
     from paper_1304_7211_gb300 import _build, rl, synth
     _build.build()
     specs = {s.name: s for s in (synth.motion(31, 0), synth.motion(31, 1), synth.disc(8),
-                                 synth.disc(12), synth.gaussian(7, 1.5), synth.motion(15, 0))}
+                                 synth.disc(12), synth.gaussian(7, 1.5), synth.motion(15, 0),
+                                 synth.motion(8, 0), synth.motion(8, 1),
+                                 synth.dense(np.eye(9)[::-1]))}
     spec = specs[args.case]
     g = synth.latent_image(args.size, args.size, synth.SEED_BASE + 2)
     f32 = np.maximum(synth.blur(g, spec), 0.0).astype(np.float32)
@@ -192,7 +194,7 @@ def run_case(args):
     f = torch.from_numpy(f32).cuda().to(dt)
     u = torch.empty_like(f)
     th = None if args.tau is None else rl.thinning(args.tau, True, 10, args.q)
-    with rl.Deconvolver(spec, path=args.path, storage=args.storage) as d:
+    with rl.Deconvolver(spec, path=args.path, storage=args.storage, adjoint=args.adjoint) as d:
         rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th)
         torch.cuda.synchronize()
         runs = [rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th,
@@ -201,7 +203,8 @@ def run_case(args):
     med = ms[len(ms) // 2]
     st = runs[-1]
     act = st.active_pixel_iterations / max(st.pixel_iterations, 1)
-    print(f"case {spec.name} {args.size}^2 x {args.iters} it {args.storage} tau={args.tau}: "
+    print(f"case {spec.name} {args.size}^2 x {args.iters} it {args.storage} tau={args.tau} "
+          f"adjoint={args.adjoint}: "
           f"{med:.3f} ms ({med / args.iters * 1e3:.1f} us/it; min {ms[0] / args.iters * 1e3:.1f}, "
           f"{len(ms)} runs) path={rl.PATH_NAME[st.path]} active={100 * act:.1f}% launches={st.launches}")
     return 0
@@ -345,6 +348,8 @@ def main():
                     help="profiling mode: run one solve of this PSF (e.g. disc8, motionx31, "
                          "motiony31, dense7x7) and print its time; no JSON line")
     ap.add_argument("--repeat", type=int, default=1, help="case mode: timed solves (median reported)")
+    ap.add_argument("--adjoint", default="padflip", choices=["padflip", "transpose"],
+                    help="case mode: adjoint of Eq. 3 (pad-flip or exact transpose)")
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--path", default="auto")
