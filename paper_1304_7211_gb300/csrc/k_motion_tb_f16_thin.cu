@@ -1,0 +1,3 @@
+// Resident running-sum kernel instantiation: storage __half, thinning true (see k_motion_tb.cuh).
+#include "k_motion_tb.cuh"
+RL_MOTION_TB_TU(launch_motion_tb_f16_thin, __half, true)

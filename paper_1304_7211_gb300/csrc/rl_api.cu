@@ -483,6 +483,7 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
     memset(&a, 0, sizeof a);
     a.clamp = ctx->boundary == RL_BOUNDARY_CLAMP;
     a.weight = ctx->weight;
+    a.transpose = needs_fold(ctx);
     rl::TBArgs tb;
     memset(&tb, 0, sizeof tb);
     tb.K = K;
@@ -751,6 +752,16 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
            "rl_iterate: counter");
         // the stale ratio of a pixel that was never used is 0
         CK(cudaMemsetAsync(ctx->rstale, 0, plane * sizeof(float), ctx->stream), "rl_iterate: stale ratio");
+    }
+    // Exact transpose of a motion PSF: the resident rows fold it along the
+    // row (every other path for it is the stencil tiles).
+    if (needs_fold(ctx) && ctx->kind == RL_PSF_MOTION && !(ctx->flags & RL_FLAG_PER_ITERATION)) {
+        const int L = ctx->axis == 0 ? ctx->kw : ctx->kh;
+        const int line = ctx->axis == 0 ? W : H;
+        if (rl::motion_x_tb_fits(line, L, thin != nullptr)) {
+            *path_out = RL_PATH_RUNSUM;
+            return run_resident(ctx, f, start, u_out, W, H, pitch, K, thin, plane, sp);
+        }
     }
     // Running sum with whole lines resident for all iterations: one launch.
     if (path == RL_PATH_RUNSUM && !(ctx->flags & RL_FLAG_PER_ITERATION)) {

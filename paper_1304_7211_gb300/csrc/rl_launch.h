@@ -23,6 +23,13 @@ cudaError_t launch_motion_x_tb(const IterArgs &a, const TBArgs &tb, int storage,
                                cudaStream_t s);
 size_t motion_x_tb_smem_bytes(int W, int L, bool thin);
 bool motion_x_tb_fits(int W, int L, bool thin);
+// per storage type and thinning mode (k_motion_tb_*.cu)
+cudaError_t launch_motion_tb_f32(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
+cudaError_t launch_motion_tb_f32_thin(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
+cudaError_t launch_motion_tb_bf16(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
+cudaError_t launch_motion_tb_bf16_thin(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
+cudaError_t launch_motion_tb_f16(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
+cudaError_t launch_motion_tb_f16_thin(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
 
 // FP64 sum of a W x H plane (pitch in elements) of the given storage into
 // *out (device); `partial` holds flux_blocks() doubles.
@@ -46,6 +53,9 @@ struct TileShape { int tx, ty; };
 TileShape tile_shape_for(int ax, int bx, int ay, int by);
 cudaError_t launch_tile(const IterArgs &a, int storage, bool thin, int mode, TileShape ts,
                         cudaStream_t s);
+cudaError_t launch_tile_f32(const IterArgs &a, bool thin, int mode, TileShape ts, cudaStream_t s);
+cudaError_t launch_tile_bf16(const IterArgs &a, bool thin, int mode, TileShape ts, cudaStream_t s);
+cudaError_t launch_tile_f16(const IterArgs &a, bool thin, int mode, TileShape ts, cudaStream_t s);
 
 // Register-blocked disc kernels (k_disc.cuh, one translation unit per
 // radius): the defocus disc of radius 1..16 with compile-time runs.  One RL

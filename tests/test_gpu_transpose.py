@@ -47,6 +47,22 @@ class Anchored:
         return oracle.psf_dense(self.t, self.anchor_x, self.anchor_y)
 
 
+class Motion:
+    """A motion PSF as the library takes it (running-sum path), with its
+    oracle taps anchored at floor(L/2)."""
+
+    def __init__(self, length, axis):
+        self.spec = synth.motion(length, axis)
+        self.kind, self.axis, self.length, self.radius = "motion", axis, length, 0
+        self.taps, self.kw, self.kh = None, 0, 0
+        self.t = self.spec.dense()
+        self.anchor_x, self.anchor_y = self.t.shape[1] // 2, self.t.shape[0] // 2
+        self.name = self.spec.name + "_motion"
+
+    def oracle_psf(self):
+        return oracle.psf_dense(self.t, self.anchor_x, self.anchor_y)
+
+
 def axis_symmetric(spec):
     t = spec.t
     return (spec.anchor_x == t.shape[1] - 1 - spec.anchor_x and spec.anchor_y == t.shape[0] - 1 - spec.anchor_y
@@ -69,6 +85,7 @@ CASES = [
     centred(synth.motion(6, 0)),
     centred(synth.motion(8, 1)),
     centred(synth.disc(3)),
+    Motion(6, 0), Motion(8, 1), Motion(9, 0),
 ]
 
 
@@ -102,10 +119,11 @@ def test_transpose_matches_oracle(spec, boundary):
         assert oracle.rel_linf(pf, ref) <= 1e-12
         assert st.path != 3 or spec.kind == "dense"
     else:
-        # not the pad-flip iterate (the test would be vacuous otherwise), and
-        # the folded transpose runs on the generic stencil tiles
+        # not the pad-flip iterate (the test would be vacuous otherwise); the
+        # fold runs in the resident rows for motion PSFs, else in the stencil
+        # tiles
         assert oracle.rel_linf(pf, ref) > 10 * TOL
-        assert st.path == 3
+        assert st.path == (1 if spec.kind == "motion" else 3)
 
 
 @pytest.mark.parametrize("shape", [(9, 11), (6, 40), (40, 6), (13, 13)])
@@ -143,11 +161,11 @@ def test_symmetric_psf_under_mirror_is_unchanged():
         assert sa.path == sb.path
 
 
+@pytest.mark.parametrize("spec", [CASES[0], Motion(6, 0), Motion(8, 1)], ids=lambda s: s.name)
 @pytest.mark.parametrize("boundary", ["mirror", "clamp"])
-def test_transpose_thinned_replay(boundary):
+def test_transpose_thinned_replay(boundary, spec):
     # the oracle's used-pixel schedule replayed: same selective convolutions
     from paper_1304_7211_gb300 import rl
-    spec = CASES[0]
     f32 = case_image(130, 90, synth.SEED_BASE + 63)
     K = 25
     ref = oracle.rl(f32.astype(np.float64), spec.oracle_psf(), K, boundary=boundary,
