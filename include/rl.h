@@ -72,7 +72,9 @@ typedef enum {
 } rl_boundary;
 
 typedef enum {
-    RL_PATH_AUTO = 0,    /* motion -> RUNSUM, disc -> SPAN, dense -> STENCIL     */
+    RL_PATH_AUTO = 0,    /* motion -> RUNSUM, disc -> SPAN; dense -> STENCIL,
+                            except uniform taps reaching more than 4 pixels
+                            from the anchor -> SPAN                             */
     RL_PATH_RUNSUM = 1,  /* sliding-window box filter along x or y (motion only)  */
     RL_PATH_SPAN = 2,    /* per-row span sums of a uniform PSF (motion, disc,
                             or dense taps that are uniform with one contiguous

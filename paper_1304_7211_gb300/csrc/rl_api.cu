@@ -35,6 +35,8 @@ struct rl_ctx {
     int kind = 0, axis = 0, disc_radius = 0;
     int kw = 0, kh = 0, ax = 0, ay = 0;  // dense layout; bx = kw-1-ax, by = kh-1-ay
     std::vector<float> taps;             // normalised, row-major kh x kw
+    std::vector<float> sq_taps;          // taps embedded in a centred K x K square (K <= 9), or empty
+    int sq_k = 0;
     bool uniform = false;                // one contiguous run of equal taps per row
     bool axis_sym = false;               // h(tx, ty) = h(-tx, ty) = h(tx, -ty)
     std::vector<int2> spans;             // per row j: [lo, hi] offsets (lo > hi = empty)
@@ -387,6 +389,22 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
     ctx->taps = tf;
     ctx->uniform = uniform;
     ctx->axis_sym = axis_sym;
+    // Taps within 4 pixels of the anchor on every side: the centred square
+    // K = 2 max(extents) + 1 with zeros around them, for the register-blocked
+    // stencil (a stencil over the square computes the same convolution).
+    {
+        const int r = std::max(std::max(ax, kw - 1 - ax), std::max(ay, kh - 1 - ay));
+        ctx->sq_taps.clear();
+        ctx->sq_k = 0;
+        if (r <= 4) {
+            const int rr = std::max(r, 1), K = 2 * rr + 1;
+            ctx->sq_taps.assign((size_t)K * K, 0.f);
+            for (int j = 0; j < kh; ++j)
+                for (int i = 0; i < kw; ++i)
+                    ctx->sq_taps[(size_t)(j - ay + rr) * K + (i - ax + rr)] = tf[(size_t)j * kw + i];
+            ctx->sq_k = K;
+        }
+    }
     ctx->spans = spans;
     ctx->weight = uniform ? (float)(common / sum) : 0.f;
     ctx->has_psf = true;
@@ -416,6 +434,10 @@ int choose_path(const rl_ctx *ctx, int W) {
     int p = ctx->path_pref;
     if (p == RL_PATH_AUTO) {
         if (ctx->kind == RL_PSF_MOTION) p = RL_PATH_RUNSUM;
+        else if (ctx->kind == RL_PSF_DISC) p = RL_PATH_SPAN;
+        // dense taps within 4 pixels of the anchor: the register-blocked
+        // stencil beats span sums (every tap a register operand)
+        else if (ctx->sq_k) p = RL_PATH_STENCIL;
         else if (ctx->uniform) p = RL_PATH_SPAN;
         else p = RL_PATH_STENCIL;
     }
@@ -676,7 +698,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     };
     auto issue = [&](int k) -> rl_status {
         const IterArgs b = args_for(k);
-        cudaError_t e = stencil_k ? rl::launch_stencil(b, ctx->taps.data(), stencil_k, ctx->storage,
+        cudaError_t e = stencil_k ? rl::launch_stencil(b, ctx->sq_taps.data(), stencil_k, ctx->storage,
                                                        thin != nullptr, ctx->qplane, sp, ctx->stream)
                                   : rl::launch_disc(b, ctx->storage, thin != nullptr, ctx->disc_radius,
                                                     ctx->qplane, sp, ctx->stream);
@@ -782,11 +804,8 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
                            ctx->disc_radius <= rl::kDiscMaxRadius;
     // centred odd square taps up to 9 x 9 take the register-blocked stencil
-    const int stencil_k = path == RL_PATH_STENCIL && !needs_fold(ctx) && ctx->kw == ctx->kh && (ctx->kw & 1) &&
-                                  ctx->kw >= 3 &&
-                                  ctx->kw <= 9 && ctx->ax == ctx->kw / 2 && ctx->ay == ctx->kh / 2
-                              ? ctx->kw
-                              : 0;
+    // taps within 4 pixels of the anchor take the register-blocked stencil
+    const int stencil_k = path == RL_PATH_STENCIL && !needs_fold(ctx) ? ctx->sq_k : 0;
     if (disc_fast || stencil_k) {
         if (ctx->q_px < plane) {
             cudaFree(ctx->qplane);

@@ -109,13 +109,15 @@ def test_asymmetric_centred_square_taps(k, boundary):
     assert oracle.rel_linf(u, ref) <= 30 * 2.0 ** -9
 
 
-def test_uniform_rectangle_from_dense_taps_uses_span_path():
-    spec = synth.dense(np.ones((3, 5)))
-    f32 = case(150, 90, spec)
-    u, st = gpu_rl(spec, f32, 40)
-    assert st.path == 2
-    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 40).u
-    assert oracle.rel_linf(u, ref) <= TOL
+def test_uniform_rectangle_from_dense_taps_auto_path():
+    # within 4 pixels of the anchor: register-blocked stencil; wider: span sums
+    for shape, path in (((3, 5), 3), ((3, 11), 2), ((13, 1), 2)):
+        spec = synth.dense(np.ones(shape))
+        f32 = case(150, 90, spec)
+        u, st = gpu_rl(spec, f32, 40)
+        assert st.path == path
+        ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 40).u
+        assert oracle.rel_linf(u, ref) <= TOL
 
 
 @pytest.mark.parametrize("spec,paths", [(synth.motion(31, 0), ("runsum", "span", "stencil")),
