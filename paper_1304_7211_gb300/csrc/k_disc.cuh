@@ -431,6 +431,24 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
         const int xb = x0 + bx * SX, yb = y0 + by * SY;
         float acc[SY][SX];
         Op::template block<FWD>(sm, by * SY, bx, acc, prm);
+        // exact transpose: band pixels of border tiles take A^T q from the band plane
+        const bool band = !FWD && a.fold_ct &&
+                          (x0 < a.fold_rx || x0 + TX > a.W - a.fold_rx || y0 < a.fold_ry || y0 + TY > a.H - a.fold_ry);
+        if (band) {
+#pragma unroll
+            for (int i = 0; i < SY; ++i) {
+                const int y = yb + i;
+#pragma unroll
+                for (int j = 0; j < SX; ++j) {
+                    const int x = xb + j;
+                    if (y < a.H && x < a.W &&
+                        (x < a.fold_rx || x >= a.W - a.fold_rx || y < a.fold_ry || y >= a.H - a.fold_ry)) {
+                        const float ct = a.fold_ct[(long long)y * q_pitch + x];
+                        acc[i][j] = Op::kUniform ? ct / a.weight : ct;
+                    }
+                }
+            }
+        }
         if (!THIN) {
             const int n = min(SX, a.W - xb);
 #pragma unroll
@@ -523,6 +541,7 @@ cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, k_disc_half<T, THIN, Op, true>, a, prm, qplane, q_pitch);
+    if (e == cudaSuccess && a.fold_ct) e = launch_fold_band(a, qplane, q_pitch, s);
     if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_disc_half<T, THIN, Op, false>, a, prm, qplane, q_pitch);
     return e;
 }

@@ -64,6 +64,8 @@ struct rl_ctx {
     float *rstale = nullptr;
     size_t thin_px = 0;
     float *qplane = nullptr;  // ratio plane of the two-launch disc path
+    float *ctplane = nullptr; // exact-transpose band of the two-launch path
+    size_t ct_bytes = 0;
     size_t q_px = 0;
     int *tflags = nullptr;    // per-tile activity of the disc path
     size_t tflags_n = 0;
@@ -219,6 +221,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->mask[1]);
     cudaFree(ctx->rstale);
     cudaFree(ctx->qplane);
+    cudaFree(ctx->ctplane);
     cudaFree(ctx->tflags);
     cudaFree(ctx->tbuf[0]);
     cudaFree(ctx->tbuf[1]);
@@ -429,8 +432,14 @@ bool needs_fold(const rl_ctx *ctx) {
 
 int choose_path(const rl_ctx *ctx, int W) {
     const int L = ctx->kind == RL_PSF_MOTION ? (ctx->axis == 0 ? ctx->kw : ctx->kh) : 0;
-    // the folded transpose is computed by the generic stencil tiles
-    if (needs_fold(ctx)) return RL_PATH_STENCIL;
+    // The exact transpose folds in the disc and register-stencil halves (a
+    // band kernel between them), in the resident motion rows (run_device)
+    // and in the generic stencil tiles, not in the span tiles.
+    if (needs_fold(ctx)) {
+        if (ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 && ctx->disc_radius <= rl::kDiscMaxRadius)
+            return RL_PATH_SPAN;
+        return RL_PATH_STENCIL;
+    }
     int p = ctx->path_pref;
     if (p == RL_PATH_AUTO) {
         if (ctx->kind == RL_PSF_MOTION) p = RL_PATH_RUNSUM;
@@ -642,6 +651,20 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     a.ax = a.bx = a.ay = a.by = R;
     a.weight = ctx->weight;
     a.m_pitch = a.mi_pitch = sp;
+    if (needs_fold(ctx)) {
+        // exact transpose: A^T q on the border band, written between the halves
+        rl_status st = grow(ctx, (void **)&ctx->ctplane, &ctx->ct_bytes, (size_t)sp * H * sizeof(float),
+                            "rl_iterate: transpose band");
+        if (st != RL_OK) return st;
+        a.fold_ct = ctx->ctplane;
+        a.fold_taps = ctx->d_taps;
+        a.fold_kw = ctx->kw;
+        a.fold_kh = ctx->kh;
+        a.fold_ax = ctx->ax;
+        a.fold_ay = ctx->ay;
+        a.fold_rx = std::max(ctx->ax, ctx->kw - 1 - ctx->ax);
+        a.fold_ry = std::max(ctx->ay, ctx->kh - 1 - ctx->ay);
+    }
     const uint8_t *sched = nullptr;
     if (thin) {
         a.relative = thin->relative != 0;
@@ -805,7 +828,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
                            ctx->disc_radius <= rl::kDiscMaxRadius;
     // centred odd square taps up to 9 x 9 take the register-blocked stencil
     // taps within 4 pixels of the anchor take the register-blocked stencil
-    const int stencil_k = path == RL_PATH_STENCIL && !needs_fold(ctx) ? ctx->sq_k : 0;
+    const int stencil_k = path == RL_PATH_STENCIL ? ctx->sq_k : 0;
     if (disc_fast || stencil_k) {
         if (ctx->q_px < plane) {
             cudaFree(ctx->qplane);

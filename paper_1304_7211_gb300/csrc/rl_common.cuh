@@ -212,6 +212,13 @@ struct IterArgs {
     int *tile_flags;                         // per tile: any pixel active next (nullable)
     int tiles_x;                             // tiles per row of tile_flags
     int transpose;                           // adjoint = exact transpose A^T (STENCIL tiles)
+    // Exact transpose on the two-half kernels: when fold_ct is set the band
+    // kernel runs between the halves and writes A^T q at the pixels within
+    // (fold_rx, fold_ry) of the border, which the adjoint half takes there.
+    float *fold_ct;                          // pitch = q plane's
+    const float *fold_taps;                  // the PSF: fold_kh x fold_kw, anchor (fold_ax, fold_ay)
+    int fold_kw, fold_kh, fold_ax, fold_ay;
+    int fold_rx, fold_ry;
 };
 
 // Several iterations in one launch (kernels that keep their lines resident).

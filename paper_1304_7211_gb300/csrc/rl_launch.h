@@ -72,6 +72,10 @@ RL_DECLARE_DISC_R(9) RL_DECLARE_DISC_R(10) RL_DECLARE_DISC_R(11) RL_DECLARE_DISC
 RL_DECLARE_DISC_R(13) RL_DECLARE_DISC_R(14) RL_DECLARE_DISC_R(15) RL_DECLARE_DISC_R(16)
 #undef RL_DECLARE_DISC_R
 
+// Exact-transpose band between the two halves (a.fold_ct set): A^T q on the
+// pixels within (fold_rx, fold_ry) of the border, from the full q plane.
+cudaError_t launch_fold_band(const IterArgs &a, const float *qplane, long long q_pitch, cudaStream_t s);
+
 // Register-blocked dense stencil (same two-launch structure as the disc):
 // centred K x K taps, K in {3, 5, 7, 9}; `taps` is a host array of K*K.
 cudaError_t launch_stencil(const IterArgs &a, const float *taps, int K, int storage, bool thin,

@@ -63,6 +63,21 @@ class Motion:
         return oracle.psf_dense(self.t, self.anchor_x, self.anchor_y)
 
 
+class Disc:
+    """A disc PSF as the library takes it (register-blocked disc kernel)."""
+
+    def __init__(self, radius):
+        self.spec = synth.disc(radius)
+        self.kind, self.axis, self.length, self.radius = "disc", 0, 0, radius
+        self.taps, self.kw, self.kh = None, 0, 0
+        self.t = self.spec.dense()
+        self.anchor_x = self.anchor_y = radius
+        self.name = self.spec.name + "_disc"
+
+    def oracle_psf(self):
+        return oracle.psf_dense(self.t, self.anchor_x, self.anchor_y)
+
+
 def axis_symmetric(spec):
     t = spec.t
     return (spec.anchor_x == t.shape[1] - 1 - spec.anchor_x and spec.anchor_y == t.shape[0] - 1 - spec.anchor_y
@@ -86,6 +101,9 @@ CASES = [
     centred(synth.motion(8, 1)),
     centred(synth.disc(3)),
     Motion(6, 0), Motion(8, 1), Motion(9, 0),
+    Disc(5),
+    # reaches 10 pixels from its anchor: the generic stencil tiles fold it
+    Anchored(asym_taps((3, 11), 5), 10, 1, "dense3x11_anchor101"),
 ]
 
 
@@ -123,7 +141,7 @@ def test_transpose_matches_oracle(spec, boundary):
         # fold runs in the resident rows for motion PSFs, else in the stencil
         # tiles
         assert oracle.rel_linf(pf, ref) > 10 * TOL
-        assert st.path == (1 if spec.kind == "motion" else 3)
+        assert st.path == {"motion": 1, "disc": 2}.get(spec.kind, 3)
 
 
 @pytest.mark.parametrize("shape", [(9, 11), (6, 40), (40, 6), (13, 13)])
@@ -161,7 +179,7 @@ def test_symmetric_psf_under_mirror_is_unchanged():
         assert sa.path == sb.path
 
 
-@pytest.mark.parametrize("spec", [CASES[0], Motion(6, 0), Motion(8, 1)], ids=lambda s: s.name)
+@pytest.mark.parametrize("spec", [CASES[0], CASES[-1], Motion(6, 0), Motion(8, 1), Disc(4)], ids=lambda s: s.name)
 @pytest.mark.parametrize("boundary", ["mirror", "clamp"])
 def test_transpose_thinned_replay(boundary, spec):
     # the oracle's used-pixel schedule replayed: same selective convolutions
