@@ -194,7 +194,8 @@ def run_case(args):
     f = torch.from_numpy(f32).cuda().to(dt)
     u = torch.empty_like(f)
     th = None if args.tau is None else rl.thinning(args.tau, True, 10, args.q)
-    with rl.Deconvolver(spec, path=args.path, storage=args.storage, adjoint=args.adjoint) as d:
+    with rl.Deconvolver(spec, path=args.path, storage=args.storage, adjoint=args.adjoint,
+                        boundary=args.boundary) as d:
         rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th)
         torch.cuda.synchronize()
         runs = [rl.rl_iterate(d.ctx, f, None, u, args.size, args.size, args.size, args.iters, th,
@@ -204,7 +205,7 @@ def run_case(args):
     st = runs[-1]
     act = st.active_pixel_iterations / max(st.pixel_iterations, 1)
     print(f"case {spec.name} {args.size}^2 x {args.iters} it {args.storage} tau={args.tau} "
-          f"adjoint={args.adjoint}: "
+          f"adjoint={args.adjoint} boundary={args.boundary}: "
           f"{med:.3f} ms ({med / args.iters * 1e3:.1f} us/it; min {ms[0] / args.iters * 1e3:.1f}, "
           f"{len(ms)} runs) path={rl.PATH_NAME[st.path]} active={100 * act:.1f}% launches={st.launches}")
     return 0
@@ -350,6 +351,8 @@ def main():
     ap.add_argument("--repeat", type=int, default=1, help="case mode: timed solves (median reported)")
     ap.add_argument("--adjoint", default="padflip", choices=["padflip", "transpose"],
                     help="case mode: adjoint of Eq. 3 (pad-flip or exact transpose)")
+    ap.add_argument("--boundary", default="mirror", choices=["mirror", "clamp"],
+                    help="case mode: boundary continuation")
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--path", default="auto")

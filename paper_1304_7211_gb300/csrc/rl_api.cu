@@ -66,6 +66,8 @@ struct rl_ctx {
     float *qplane = nullptr;  // ratio plane of the two-launch disc path
     float *ctplane = nullptr; // exact-transpose band of the two-launch path
     size_t ct_bytes = 0;
+    float *zplane = nullptr;  // its apron values (extended plane)
+    size_t z_bytes = 0;
     size_t q_px = 0;
     int *tflags = nullptr;    // per-tile activity of the disc path
     size_t tflags_n = 0;
@@ -222,6 +224,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->rstale);
     cudaFree(ctx->qplane);
     cudaFree(ctx->ctplane);
+    cudaFree(ctx->zplane);
     cudaFree(ctx->tflags);
     cudaFree(ctx->tbuf[0]);
     cudaFree(ctx->tbuf[1]);
@@ -664,6 +667,11 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         a.fold_ay = ctx->ay;
         a.fold_rx = std::max(ctx->ax, ctx->kw - 1 - ctx->ax);
         a.fold_ry = std::max(ctx->ay, ctx->kh - 1 - ctx->ay);
+        a.fold_zp = (long long)W + ctx->kw - 1;
+        st = grow(ctx, (void **)&ctx->zplane, &ctx->z_bytes,
+                  (size_t)a.fold_zp * (H + ctx->kh - 1) * sizeof(float), "rl_iterate: transpose apron");
+        if (st != RL_OK) return st;
+        a.fold_z = ctx->zplane;
     }
     const uint8_t *sched = nullptr;
     if (thin) {

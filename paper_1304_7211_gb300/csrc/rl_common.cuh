@@ -219,6 +219,8 @@ struct IterArgs {
     const float *fold_taps;                  // the PSF: fold_kh x fold_kw, anchor (fold_ax, fold_ay)
     int fold_kw, fold_kh, fold_ax, fold_ay;
     int fold_rx, fold_ry;
+    float *fold_z;                           // z on the apron, extended plane
+    long long fold_zp;                       // its pitch: W + kw - 1
 };
 
 // Several iterations in one launch (kernels that keep their lines resident).
