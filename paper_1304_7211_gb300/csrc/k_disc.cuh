@@ -349,6 +349,27 @@ __device__ __forceinline__ void st_seg(T *p, int n, const float (&v)[SX]) {
         if (j < n) Stor<T>::st(p, j, v[j]);
 }
 
+// Eight bytes of a mask row segment (byte j = pixel j, non-zero = active) as
+// one 8-byte access when whole and aligned, else the first n bytes.
+__device__ __forceinline__ unsigned long long ld_mask8(const uint8_t *p, int n) {
+    if (n == SX && (reinterpret_cast<uintptr_t>(p) & 7) == 0) return *reinterpret_cast<const unsigned long long *>(p);
+    unsigned long long v = 0;
+#pragma unroll
+    for (int j = 0; j < SX; ++j)
+        if (j < n) v |= (unsigned long long)p[j] << (8 * j);
+    return v;
+}
+
+__device__ __forceinline__ void st_mask8(uint8_t *p, int n, unsigned long long v) {
+    if (n == SX && (reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+        *reinterpret_cast<unsigned long long *>(p) = v;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < SX; ++j)
+        if (j < n) p[j] = (uint8_t)(v >> (8 * j));
+}
+
 // One half of an RL iteration for a TX x TY output tile (128 threads, one
 // SY x SX block each).  FWD: v = h (x) u and q = f / v on the tile, written
 // to the q plane (inactive pixels keep their q: it is the ratio of their last
@@ -376,6 +397,7 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
+    bool tile_any = false;  // a pixel of this thread's blocks stays active
     // Selective convolution at tile granularity: a tile none of whose pixels
     // is active does nothing (u stays, q keeps the stale ratios).
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + blockIdx.y * a.tiles_x + blockIdx.x : nullptr;
@@ -472,53 +494,63 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
             }
             continue;
         }
+        // selective convolution (Eq. 4-5), one row segment of SX pixels at a
+        // time: mask bytes as one 8-byte access, f / u and u' as 16-byte ones
+        const int n = min(SX, a.W - xb);
 #pragma unroll
         for (int i = 0; i < SY; ++i) {
             const int y = yb + i;
-            if (y >= a.H) break;
+            if (y >= a.H || n <= 0) break;
+            const unsigned long long ones = 0x0101010101010101ull;
+            const unsigned long long m =
+                a.full ? ones : ld_mask8(a.mask_in + (long long)y * a.mi_pitch + xb, n);
+            if (FWD) {
+                if (m == 0) continue;  // no pixel of the segment used: q keeps its stale ratios
+                float e[SX], o[SX];
+                ld_seg<T>((const T *)a.f + (long long)y * a.f_pitch + xb, n, e);
 #pragma unroll
-            for (int j = 0; j < SX; ++j) {
-                const int x = xb + j;
-                if (x >= a.W) break;
-                if (FWD) {
-                    bool use = true;
-                    if (THIN && !a.full) use = a.mask_in[(long long)y * a.mi_pitch + x] != 0;
-                    if (use) {
-                        const float fv = Stor<T>::ld((const T *)a.f, (long long)y * a.f_pitch + x);
-                        qplane[(long long)y * q_pitch + x] = rl_ratio(fv, (Op::kUniform ? acc[i][j] * a.weight : acc[i][j]));
-                    }
+                for (int j = 0; j < SX; ++j)
+                    o[j] = rl_ratio(e[j], Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
+                float *qrow = qplane + (long long)y * q_pitch + xb;
+                if (m == ones) {
+                    st_seg<float>(qrow, n, o);
                 } else {
-                    const float u = Stor<T>::ld((const T *)a.u_in, (long long)y * a.in_pitch + x);
-                    const float c = (Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
-                    float un = u * c;
-                    if (THIN) {
-                        const bool use = a.full || a.mask_in[(long long)y * a.mi_pitch + x] != 0;
-                        used += use;
-                        un = use ? un : u;
-                        if (a.update_mask && !a.replay) {
-                            float d = 0.f;
-                            if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
-                            a.mask_out[(long long)y * a.m_pitch + x] = (uint8_t)(use && d >= a.tau);
-                        }
-                    }
-                    Stor<T>::st((T *)a.u_out, (long long)y * a.out_pitch + x, un);
+#pragma unroll
+                    for (int j = 0; j < SX; ++j)
+                        if (j < n && ((m >> (8 * j)) & 0xff)) qrow[j] = o[j];
+                }
+            } else {
+                float uv[SX], o[SX];
+                ld_seg<T>((const T *)a.u_in + (long long)y * a.in_pitch + xb, n, uv);
+                unsigned long long mo = 0;
+#pragma unroll
+                for (int j = 0; j < SX; ++j) {
+                    const float u = uv[j];
+                    const float c = Op::kUniform ? acc[i][j] * a.weight : acc[i][j];
+                    const bool use = ((m >> (8 * j)) & 0xff) != 0;
+                    const float un = use ? u * c : u;
+                    o[j] = un;
+                    if (j < n) used += use;
+                    float d = 0.f;
+                    if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
+                    mo |= (unsigned long long)(use && d >= a.tau) << (8 * j);
+                }
+                st_seg<T>((T *)a.u_out + (long long)y * a.out_pitch + xb, n, o);
+                if (n < SX) mo &= (1ull << (8 * n)) - 1ull;  // bytes past the row end
+                if (a.update_mask && !a.replay) {
+                    st_mask8(a.mask_out + (long long)y * a.m_pitch + xb, n, mo);
+                    tile_any |= mo != 0;
                 }
             }
         }
     }
-    const int xb = x0 + nbx * SX, yb = y0 + nby * SY;
     if (!FWD && THIN) {
         if (a.active_count) warp_count_add(a.active_count, used);
         if (tflag && a.update_mask) {
             // does any pixel of the tile stay active for the next iteration?
-            bool any = false;
-            for (int i = 0; i < SY; ++i)
-                for (int j = 0; j < SX; ++j) {
-                    const int y = yb + i, x = xb + j;
-                    if (y < a.H && x < a.W) any |= a.mask_out[(long long)y * a.m_pitch + x] != 0;
-                }
-            const int n = __syncthreads_count(any);
-            if (threadIdx.x == 0) *tflag = n;
+            // (blocks not processed had no active pixel and keep mask 0)
+            const int cnt = __syncthreads_count(tile_any);
+            if (threadIdx.x == 0) *tflag = cnt;
         }
     }
 }
