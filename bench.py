@@ -480,7 +480,7 @@ def main():
         achieved = flops / (launch_ms * 1e-3) / 1e12
         # DRAM bytes of one iteration (both launches) from the ncu capture
         # summarised in profiles/k_disc_half_disc8_2048.md (cold-cache reads)
-        traffic = 33.597952e6 + 0.001536e6 + 33.586944e6 + 0.0
+        traffic = 33.596928e6 + 0.003328e6 + 33.604352e6 + 0.0
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": f"k_disc_half<float,0,DiscOp<8>,FWD>+<..,ADJ> ({dom}, both launches of one iteration)",
