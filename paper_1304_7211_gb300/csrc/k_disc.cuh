@@ -97,8 +97,25 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
                 const int r = e / nu, u = e - r * nu;
                 const T *srow = src + (long long)bmap(y0 + r, H, clamp) * sp;
                 const int x = xs + 4 * u;
+                if (x >= 0 && x + 4 <= W && (reinterpret_cast<uintptr_t>(srow + x) & 7) == 0) {
+                    // a whole unit inside the image: one 8-byte load of 4 values
+                    const uint2 w2 = __ldg(reinterpret_cast<const uint2 *>(srow + x));
+                    const unsigned wv[2] = {w2.x, w2.y};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) v[b][k] = Stor<T>::ld(srow, bmap(x + k, W, clamp));
+                    for (int k = 0; k < 2; ++k) {
+                        const unsigned short lo = (unsigned short)(wv[k] & 0xffffu), hi = (unsigned short)(wv[k] >> 16);
+                        if constexpr (std::is_same<T, __half>::value) {
+                            v[b][2 * k] = __half2float(__ushort_as_half(lo));
+                            v[b][2 * k + 1] = __half2float(__ushort_as_half(hi));
+                        } else {
+                            v[b][2 * k] = __bfloat162float(__ushort_as_bfloat16(lo));
+                            v[b][2 * k + 1] = __bfloat162float(__ushort_as_bfloat16(hi));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) v[b][k] = Stor<T>::ld(srow, bmap(x + k, W, clamp));
+                }
             }
         }
 #pragma unroll
