@@ -1,24 +1,30 @@
-// k_disc.cuh -- register-blocked generic box filter for the defocus disc
-// (Sec. 3 "Defocus blur"), one fused RL iteration (Eq. 3) per launch.
+// k_disc.cuh -- the register-blocked two-half RL iteration (Eq. 3): the
+// generic box filter for the defocus disc (Sec. 3 "Defocus blur") and the
+// direct stencil for taps within 4 pixels of the anchor, one output tile per
+// CTA, a block operation policy for the convolution.
 //
-// The disc of radius R (pixel-centre inclusion) is a stack of horizontal runs:
-// PSF row ty covers tx in [-s(ty), s(ty)], s(ty) = floor(sqrt(R^2 - ty^2)).
-// Each thread owns a block of SY x SX outputs.  For every input row the block
-// touches, it loads the row segment [x0 - R, x0 + SX + R) once from shared
-// memory, forms its running (prefix) sum in registers -- short, so FP32
-// stays accurate -- and adds to each output row that uses this input row the
-// run sum P[j + R + 1 + s] - P[j + R - s]: sliding the PSF only exchanges the
-// run ends (Sec. 3), and with a prefix a run of any length costs one
-// difference.  R is a template parameter, so every run end is a compile-time
-// register index; the disc is symmetric, so the forward convolution and the
-// adjoint (h* = h reflected) use the same table.
+// Disc (DiscOp<R>): the disc of radius R (pixel-centre inclusion) is a stack
+// of horizontal runs; PSF row ty covers tx in [-s(ty), s(ty)],
+// s(ty) = floor(sqrt(R^2 - ty^2)).  Each thread owns a block of SY x SX
+// outputs.  For every input row the block touches, it loads the row segment
+// [x0 - R, x0 + SX + R) once from shared memory, forms its running (prefix)
+// sum in registers -- short, so FP32 stays accurate -- and adds to each
+// output row that uses this input row the run sum P[j + R + 1 + s] -
+// P[j + R - s]: sliding the PSF only exchanges the run ends (Sec. 3), and
+// with a prefix a run of any length costs one difference.  R is a template
+// parameter, so every run end is a compile-time register index; the disc is
+// symmetric, so the forward convolution and the adjoint (h* = h reflected)
+// use the same table.  Stencil (StencilOp<K>): K x K taps in the kernel's
+// parameter block, each a constant-bank FMA operand at a compile-time window
+// offset.
 //
 // The iteration runs as two launches (forward + ratio into a q plane, then
-// adjoint + update): the disc path is bound by arithmetic, not HBM, so the
-// second 12 B/px of traffic is cheaper than recomputing the forward
-// convolution over a 2R apron, and each launch stages a single halo'd array
-// (more resident CTAs).  The q plane doubles as the stale ratio of Eq. 5:
-// inactive pixels are simply not rewritten.
+// adjoint + update in place): the second 12 B/px of traffic is cheaper than
+// recomputing the forward convolution over a 2R apron, and each launch
+// stages a single halo'd array (more resident CTAs).  The q plane doubles as
+// the stale ratio of Eq. 5: inactive pixels are simply not rewritten.  With
+// the exact-transpose adjoint, a band kernel between the halves (k_fold.cu)
+// supplies A^T q on the border band.
 #pragma once
 
 #include <type_traits>
