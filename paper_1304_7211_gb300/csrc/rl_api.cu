@@ -44,9 +44,13 @@ struct rl_ctx {
     float *d_taps = nullptr;
     int2 *d_spans = nullptr;
     size_t taps_cap = 0, spans_cap = 0;
-    char *h_psf = nullptr;        // pinned staging of taps + spans
-    size_t h_psf_cap = 0;
-    cudaEvent_t ev_psf = nullptr; // last PSF upload
+    // pinned staging of taps + spans: a ring, so that a new upload waits only
+    // for the one kPsfRing uploads back, not for the work queued since
+    static constexpr int kPsfRing = 4;
+    char *h_psf[kPsfRing] = {};
+    size_t h_psf_cap[kPsfRing] = {};
+    cudaEvent_t ev_psf[kPsfRing] = {};
+    int psf_slot = 0;
     // The legacy / per-thread default stream cannot be captured into a CUDA
     // graph: for a context created on it, rl_iterate runs on this internal
     // non-blocking stream, fenced by events to the caller's stream.
@@ -120,14 +124,21 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Scratch growth in stream order on the context stream: the old buffer is
+// released after the work already queued there, and no other stream (of a
+// batch, say) is waited on, as cudaFree would.
 rl_status grow(rl_ctx *ctx, void **p, size_t *have, size_t need, const char *what) {
     if (*have >= need && *p) return RL_OK;
-    if (*p) cudaFree(*p);
+    if (*p) cudaFreeAsync(*p, ctx->stream);
     *p = nullptr;
     *have = 0;
-    CK(cudaMalloc(p, need), what);
+    CK(cudaMallocAsync(p, need, ctx->stream), what);
     *have = need;
     return RL_OK;
+}
+
+void sfree(rl_ctx *ctx, void *p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
 }
 
 }  // namespace
@@ -192,7 +203,8 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flux, (rl::flux_blocks() + 2) * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_psf, cudaEventDisableTiming);
+    for (int i = 0; i < rl_ctx::kPsfRing && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ctx->ev_psf[i], cudaEventDisableTiming);
     if (e == cudaSuccess && (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy ||
                              ctx->stream == cudaStreamPerThread)) {
         e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
@@ -215,6 +227,10 @@ rl_status rl_destroy(rl_ctx *ctx) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
+    // Scratch comes from the stream-ordered pool: let the work queued on the
+    // context's streams finish before any of it is released.
+    if (ctx->own) cudaStreamSynchronize(ctx->own);
+    cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->d_taps);
     cudaFree(ctx->d_spans);
     cudaFree(ctx->ubuf[0]);
@@ -234,11 +250,13 @@ rl_status rl_destroy(rl_ctx *ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->stage[i]);
     cudaFree(ctx->sched);
-    if (ctx->ev_psf) {
-        cudaEventSynchronize(ctx->ev_psf);
-        cudaEventDestroy(ctx->ev_psf);
+    for (int i = 0; i < rl_ctx::kPsfRing; ++i) {
+        if (ctx->ev_psf[i]) {
+            cudaEventSynchronize(ctx->ev_psf[i]);
+            cudaEventDestroy(ctx->ev_psf[i]);
+        }
+        if (ctx->h_psf[i]) cudaFreeHost(ctx->h_psf[i]);
     }
-    if (ctx->h_psf) cudaFreeHost(ctx->h_psf);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->own) {
@@ -338,47 +356,48 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
             axis_sym = v == t[(size_t)j * kw + (kw - 1 - i)] && v == t[(size_t)(kh - 1 - j) * kw + i];
         }
 
-    // Stream-ordered upload through a pinned staging buffer; device buffers
-    // only grow, so changing the PSF between calls neither allocates nor
-    // synchronises the device (work already queued keeps the old taps).
+    // Stream-ordered upload through a ring of pinned staging buffers; device
+    // buffers only grow, and grow in stream order (cudaFreeAsync /
+    // cudaMallocAsync on the context stream), so changing the PSF between
+    // calls neither synchronises the device nor waits for queued work (which
+    // keeps the old taps).
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     const size_t tb = tf.size() * sizeof(float), sb = spans.size() * sizeof(int2);
     cudaError_t e = cudaSuccess;
     if (ctx->taps_cap < tb) {
-        cudaFree(ctx->d_taps);
+        if (ctx->d_taps) cudaFreeAsync(ctx->d_taps, ctx->stream);
         ctx->d_taps = nullptr;
         ctx->taps_cap = 0;
-        e = cudaMalloc(&ctx->d_taps, tb);
+        e = cudaMallocAsync((void **)&ctx->d_taps, tb, ctx->stream);
         if (e == cudaSuccess) ctx->taps_cap = tb;
     }
     if (e == cudaSuccess && ctx->spans_cap < sb) {
-        cudaFree(ctx->d_spans);
+        if (ctx->d_spans) cudaFreeAsync(ctx->d_spans, ctx->stream);
         ctx->d_spans = nullptr;
         ctx->spans_cap = 0;
-        e = cudaMalloc(&ctx->d_spans, sb);
+        e = cudaMallocAsync((void **)&ctx->d_spans, sb, ctx->stream);
         if (e == cudaSuccess) ctx->spans_cap = sb;
     }
-    if (e == cudaSuccess && ctx->h_psf_cap < tb + sb) {
-        if (ctx->h_psf) {
-            cudaEventSynchronize(ctx->ev_psf);
-            cudaFreeHost(ctx->h_psf);
-        }
-        ctx->h_psf = nullptr;
-        ctx->h_psf_cap = 0;
-        e = cudaMallocHost((void **)&ctx->h_psf, tb + sb);
-        if (e == cudaSuccess) ctx->h_psf_cap = tb + sb;
+    const int rs = ctx->psf_slot;
+    ctx->psf_slot = (rs + 1) % rl_ctx::kPsfRing;
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_psf[rs]);  // this staging buffer free again
+    if (e == cudaSuccess && ctx->h_psf_cap[rs] < tb + sb) {
+        if (ctx->h_psf[rs]) cudaFreeHost(ctx->h_psf[rs]);
+        ctx->h_psf[rs] = nullptr;
+        ctx->h_psf_cap[rs] = 0;
+        e = cudaMallocHost((void **)&ctx->h_psf[rs], tb + sb);
+        if (e == cudaSuccess) ctx->h_psf_cap[rs] = tb + sb;
     }
-    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_psf);  // staging buffer free again
     if (e == cudaSuccess) {
-        memcpy(ctx->h_psf, tf.data(), tb);
-        memcpy(ctx->h_psf + tb, spans.data(), sb);
-        e = cudaMemcpyAsync(ctx->d_taps, ctx->h_psf, tb, cudaMemcpyHostToDevice, ctx->stream);
+        memcpy(ctx->h_psf[rs], tf.data(), tb);
+        memcpy(ctx->h_psf[rs] + tb, spans.data(), sb);
+        e = cudaMemcpyAsync(ctx->d_taps, ctx->h_psf[rs], tb, cudaMemcpyHostToDevice, ctx->stream);
     }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->d_spans, ctx->h_psf + tb, sb, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_psf, ctx->stream);
+        e = cudaMemcpyAsync(ctx->d_spans, ctx->h_psf[rs] + tb, sb, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_psf[rs], ctx->stream);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
         ctx->has_psf = false;
@@ -567,12 +586,12 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
     } else {
         const size_t tbytes = (size_t)Ht * tp * es;
         if (ctx->tbuf_bytes < tbytes) {
-            cudaFree(ctx->tbuf[0]);
-            cudaFree(ctx->tbuf[1]);
+            sfree(ctx, ctx->tbuf[0]);
+            sfree(ctx, ctx->tbuf[1]);
             ctx->tbuf[0] = ctx->tbuf[1] = nullptr;
             ctx->tbuf_bytes = 0;
-            CK(cudaMalloc(&ctx->tbuf[0], tbytes), "rl_iterate: transposed f");
-            CK(cudaMalloc(&ctx->tbuf[1], tbytes), "rl_iterate: transposed u");
+            CK(cudaMallocAsync(&ctx->tbuf[0], tbytes, ctx->stream), "rl_iterate: transposed f");
+            CK(cudaMallocAsync(&ctx->tbuf[1], tbytes, ctx->stream), "rl_iterate: transposed u");
             ctx->tbuf_bytes = tbytes;
         }
         CK(rl::launch_transpose(f, pitch, 0, ctx->tbuf[0], tp, 0, W, H, 1, (int)es, ctx->stream),
@@ -636,12 +655,12 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     const size_t es = elem_size(ctx->storage);
     const size_t plane = (size_t)sp * H;
     if (ctx->ubuf_bytes < plane * es) {
-        cudaFree(ctx->ubuf[0]);
-        cudaFree(ctx->ubuf[1]);
+        sfree(ctx, ctx->ubuf[0]);
+        sfree(ctx, ctx->ubuf[1]);
         ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
         ctx->ubuf_bytes = 0;
-        CK(cudaMalloc(&ctx->ubuf[0], plane * es), "rl_iterate: scratch u");
-        CK(cudaMalloc(&ctx->ubuf[1], plane * es), "rl_iterate: scratch u");
+        CK(cudaMallocAsync(&ctx->ubuf[0], plane * es, ctx->stream), "rl_iterate: scratch u");
+        CK(cudaMallocAsync(&ctx->ubuf[1], plane * es, ctx->stream), "rl_iterate: scratch u");
         ctx->ubuf_bytes = plane * es;
     }
     IterArgs a;
@@ -695,10 +714,10 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
             const int tx = (W + 63) / 64, ty = (H + 63) / 64;
             const size_t n = (size_t)tx * ty;
             if (ctx->tflags_n < n) {
-                cudaFree(ctx->tflags);
+                sfree(ctx, ctx->tflags);
                 ctx->tflags = nullptr;
                 ctx->tflags_n = 0;
-                CK(cudaMalloc(&ctx->tflags, n * sizeof(int)), "rl_iterate: tile flags");
+                CK(cudaMallocAsync((void **)&ctx->tflags, n * sizeof(int), ctx->stream), "rl_iterate: tile flags");
                 ctx->tflags_n = n;
             }
             a.tile_flags = ctx->tflags;
@@ -789,16 +808,16 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     if (thin) {
         if (ctx->thin_px < plane) {
             for (int i = 0; i < 2; ++i) {
-                cudaFree(ctx->mask[i]);
+                sfree(ctx, ctx->mask[i]);
                 ctx->mask[i] = nullptr;
             }
-            cudaFree(ctx->rstale);
+            sfree(ctx, ctx->rstale);
             ctx->rstale = nullptr;
             ctx->thin_px = 0;
             ctx->last_mask = nullptr;
-            CK(cudaMalloc(&ctx->mask[0], plane), "rl_iterate: mask");
-            CK(cudaMalloc(&ctx->mask[1], plane), "rl_iterate: mask");
-            CK(cudaMalloc(&ctx->rstale, plane * sizeof(float)), "rl_iterate: stale ratio");
+            CK(cudaMallocAsync((void **)&ctx->mask[0], plane, ctx->stream), "rl_iterate: mask");
+            CK(cudaMallocAsync((void **)&ctx->mask[1], plane, ctx->stream), "rl_iterate: mask");
+            CK(cudaMallocAsync((void **)&ctx->rstale, plane * sizeof(float), ctx->stream), "rl_iterate: stale ratio");
             ctx->thin_px = plane;
         }
         CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream),
@@ -824,12 +843,12 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             return run_resident(ctx, f, start, u_out, W, H, pitch, K, thin, plane, sp);
     }
     if ((K > 1 || u_out == start) && ctx->ubuf_bytes < plane * es) {
-        cudaFree(ctx->ubuf[0]);
-        cudaFree(ctx->ubuf[1]);
+        sfree(ctx, ctx->ubuf[0]);
+        sfree(ctx, ctx->ubuf[1]);
         ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
         ctx->ubuf_bytes = 0;
-        CK(cudaMalloc(&ctx->ubuf[0], plane * es), "rl_iterate: scratch u");
-        CK(cudaMalloc(&ctx->ubuf[1], plane * es), "rl_iterate: scratch u");
+        CK(cudaMallocAsync(&ctx->ubuf[0], plane * es, ctx->stream), "rl_iterate: scratch u");
+        CK(cudaMallocAsync(&ctx->ubuf[1], plane * es, ctx->stream), "rl_iterate: scratch u");
         ctx->ubuf_bytes = plane * es;
     }
     const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
@@ -839,10 +858,10 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     const int stencil_k = path == RL_PATH_STENCIL ? ctx->sq_k : 0;
     if (disc_fast || stencil_k) {
         if (ctx->q_px < plane) {
-            cudaFree(ctx->qplane);
+            sfree(ctx, ctx->qplane);
             ctx->qplane = nullptr;
             ctx->q_px = 0;
-            CK(cudaMalloc(&ctx->qplane, plane * sizeof(float)), "rl_iterate: ratio plane");
+            CK(cudaMallocAsync((void **)&ctx->qplane, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
             ctx->q_px = plane;
         }
         if (thin) CK(cudaMemsetAsync(ctx->qplane, 0, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
