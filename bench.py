@@ -211,10 +211,11 @@ def run_case(args):
     return 0
 
 
-def batch_run(local, n_images=64, slots=8):
+def batch_run(local, n_images=64, slots=32):
     """Batched workload: 64 images, sides log-uniform in [128, 1536], PSF and
     iteration count (50..300) per image, all submitted to one rl_batch
-    (8 streams) vs the same solves one at a time.  Returns a dict."""
+    (32 streams: small images fill few CTA slots each) vs the same solves one
+    at a time.  Returns a dict."""
     import numpy as np
     import torch
     from paper_1304_7211_gb300 import rl, synth
@@ -256,7 +257,7 @@ def batch_run(local, n_images=64, slots=8):
             "timing": "host wall clock around submit..sync, inputs resident"}
 
 
-def serve_run(local, n=200, rate=100.0, slots=8):
+def serve_run(local, n=200, rate=100.0, slots=16):
     """Served workload: a Poisson-arrival trace (rate req/s), sides
     log-uniform in [256, 4096], PSF as in the batched workload, 50..500
     iterations, thinning threshold 1e-4 (mask recomputed every 10
