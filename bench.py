@@ -187,6 +187,8 @@ def run_case(args):
                                  synth.disc(12), synth.gaussian(7, 1.5), synth.motion(15, 0),
                                  synth.motion(8, 0), synth.motion(8, 1),
                                  synth.dense(np.eye(9)[::-1]))}
+    # uniform centred squares (register-blocked box kernel)
+    specs.update({f"box{k}": synth.dense(np.ones((k, k))) for k in (3, 9, 17, 33)})
     spec = specs[args.case]
     g = synth.latent_image(args.size, args.size, synth.SEED_BASE + 2)
     f32 = np.maximum(synth.blur(g, spec), 0.0).astype(np.float32)

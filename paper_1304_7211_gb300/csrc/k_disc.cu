@@ -1,4 +1,4 @@
-// k_disc.cu -- radius / size dispatch of the register-blocked disc and stencil kernels.
+// k_disc.cu -- radius / size dispatch of the register-blocked disc, box and stencil kernels.
 #include "rl_launch.h"
 
 namespace rl {
@@ -13,6 +13,20 @@ cudaError_t launch_disc(const IterArgs &a, int storage, bool thin, int radius, f
     RL_DISC_CASE(11) RL_DISC_CASE(12) RL_DISC_CASE(13) RL_DISC_CASE(14) RL_DISC_CASE(15)
     RL_DISC_CASE(16)
 #undef RL_DISC_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_box(const IterArgs &a, int storage, bool thin, int radius, float *qplane, long long q_pitch,
+                       cudaStream_t s) {
+    switch (radius) {
+#define RL_BOX_CASE(R) \
+    case R: return launch_box_r##R(a, storage, thin, qplane, q_pitch, s);
+    RL_BOX_CASE(1) RL_BOX_CASE(2) RL_BOX_CASE(3) RL_BOX_CASE(4) RL_BOX_CASE(5)
+    RL_BOX_CASE(6) RL_BOX_CASE(7) RL_BOX_CASE(8) RL_BOX_CASE(9) RL_BOX_CASE(10)
+    RL_BOX_CASE(11) RL_BOX_CASE(12) RL_BOX_CASE(13) RL_BOX_CASE(14) RL_BOX_CASE(15)
+    RL_BOX_CASE(16)
+#undef RL_BOX_CASE
     }
     return cudaErrorInvalidValue;
 }

@@ -263,6 +263,81 @@ struct DiscOp {
     }
 };
 
+// Horizontal box sums of one staged row: h[j] = sum of the 2R + 1 window
+// values centred on column j of the block (a sliding sum).
+template <int R>
+__device__ __forceinline__ void box_row(const float *row, int bx, float (&h)[SX]) {
+    constexpr int NW = SX + 2 * R;
+    float w[NW];
+    load_window<R>(row, bx, w);
+    float s = w[0];
+#pragma unroll
+    for (int k = 1; k <= 2 * R; ++k) s += w[k];
+    h[0] = s;
+#pragma unroll
+    for (int j = 1; j < SX; ++j) {
+        s += w[j + 2 * R] - w[j - 1];
+        h[j] = s;
+    }
+}
+
+// Uniform (2R + 1)^2 box: separable sums.  Output row i adds the box sums of
+// input rows i..i + 2R.  Rows SY - 1..2R are common to all SY outputs and
+// summed once; the 2 (SY - 1) edge rows go to the outputs that reach them.
+template <int R>
+__device__ __forceinline__ void box_block(const float *tile, int row0, int bx, float (&out)[SY][SX]) {
+    using G = Halo<R>;
+    static_assert(2 * R + 1 >= SY - 1, "the top and bottom edge rows must not overlap");
+    const float *base = tile + row0 * G::HP;
+    float c[SX];
+    if constexpr (2 * R >= SY - 1) {
+        box_row<R>(base + (SY - 1) * G::HP, bx, c);
+    } else {  // no common row (R = 1)
+#pragma unroll
+        for (int j = 0; j < SX; ++j) c[j] = 0.f;
+    }
+#pragma unroll(R > 8 ? 2 : 1)  // two rows in flight where the register cap allows
+    for (int m = SY; m <= 2 * R; ++m) {
+        float h[SX];
+        box_row<R>(base + m * G::HP, bx, h);
+#pragma unroll
+        for (int j = 0; j < SX; ++j) c[j] += h[j];
+    }
+#pragma unroll
+    for (int i = 0; i < SY; ++i)
+#pragma unroll
+        for (int j = 0; j < SX; ++j) out[i][j] = c[j];
+    // edge row e < SY - 1 reaches outputs 0..e; edge row 2R + e (e >= 1)
+    // reaches outputs e..SY - 1
+#pragma unroll
+    for (int e = 0; e < SY - 1; ++e) {
+        float h[SX];
+        box_row<R>(base + e * G::HP, bx, h);
+#pragma unroll
+        for (int i = 0; i <= e; ++i)
+#pragma unroll
+            for (int j = 0; j < SX; ++j) out[i][j] += h[j];
+        box_row<R>(base + (2 * R + 1 + e) * G::HP, bx, h);
+#pragma unroll
+        for (int i = e + 1; i < SY; ++i)
+#pragma unroll
+            for (int j = 0; j < SX; ++j) out[i][j] += h[j];
+    }
+}
+
+// Uniform (2R + 1)^2 box (Sec. 3, rectangular blur).
+template <int R>
+struct BoxOp {
+    static constexpr int kR = R;
+    static constexpr bool kUniform = true;
+    struct Params {};
+    template <bool FWD>
+    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
+                                                 const Params &) {
+        box_block<R>(tile, row0, bx, acc);  // symmetric: forward = adjoint
+    }
+};
+
 // Dense K x K taps centred on the origin (naive spatial convolution / list
 // filter of Sec. 3 and 5): every tap is a compile-time offset into the
 // register window and a constant-bank operand of its FMA.
@@ -625,6 +700,14 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
     cudaError_t launch_disc_r##R(const IterArgs &a, int storage, bool thin, float *qplane,   \
                                  long long q_pitch, cudaStream_t s) {                        \
         return disc::launch_op<disc::DiscOp<R>>(a, {}, storage, thin, qplane, q_pitch, s);  \
+    }                                                                                        \
+    }
+
+#define RL_BOX_TU(R)                                                                         \
+    namespace rl {                                                                           \
+    cudaError_t launch_box_r##R(const IterArgs &a, int storage, bool thin, float *qplane,    \
+                                long long q_pitch, cudaStream_t s) {                         \
+        return disc::launch_op<disc::BoxOp<R>>(a, {}, storage, thin, qplane, q_pitch, s);   \
     }                                                                                        \
     }
 

@@ -37,6 +37,7 @@ struct rl_ctx {
     std::vector<float> taps;             // normalised, row-major kh x kw
     std::vector<float> sq_taps;          // taps embedded in a centred K x K square (K <= 9), or empty
     int sq_k = 0;
+    int box_radius = 0;                  // uniform centred (2R + 1)^2 square, R <= 16, else 0
     bool uniform = false;                // one contiguous run of equal taps per row
     bool axis_sym = false;               // h(tx, ty) = h(-tx, ty) = h(tx, -ty)
     std::vector<int2> spans;             // per row j: [lo, hi] offsets (lo > hi = empty)
@@ -430,6 +431,14 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
             ctx->sq_k = K;
         }
     }
+    // A uniform centred odd square: the register-blocked box (separable sums).
+    ctx->box_radius = 0;
+    if (uniform && kw == kh && (kw & 1) && ax == kw / 2 && ay == kh / 2 && kw / 2 >= 1 &&
+        kw / 2 <= rl::kDiscMaxRadius) {
+        bool full = true;
+        for (int j = 0; j < kh && full; ++j) full = spans[j].x == -ax && spans[j].y == kw - 1 - ax;
+        if (full) ctx->box_radius = kw / 2;
+    }
     ctx->spans = spans;
     ctx->weight = uniform ? (float)(common / sum) : 0.f;
     ctx->has_psf = true;
@@ -454,18 +463,22 @@ bool needs_fold(const rl_ctx *ctx) {
 
 int choose_path(const rl_ctx *ctx, int W) {
     const int L = ctx->kind == RL_PSF_MOTION ? (ctx->axis == 0 ? ctx->kw : ctx->kh) : 0;
-    // The exact transpose folds in the disc and register-stencil halves (a
-    // band kernel between them), in the resident motion rows (run_device)
+    // The exact transpose folds in the disc, box and register-stencil halves
+    // (a band kernel between them), in the resident motion rows (run_device)
     // and in the generic stencil tiles, not in the span tiles.
     if (needs_fold(ctx)) {
         if (ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 && ctx->disc_radius <= rl::kDiscMaxRadius)
             return RL_PATH_SPAN;
+        if (ctx->box_radius) return RL_PATH_SPAN;
         return RL_PATH_STENCIL;
     }
     int p = ctx->path_pref;
     if (p == RL_PATH_AUTO) {
         if (ctx->kind == RL_PSF_MOTION) p = RL_PATH_RUNSUM;
         else if (ctx->kind == RL_PSF_DISC) p = RL_PATH_SPAN;
+        // a uniform centred square: separable box sums beat the stencil's
+        // K^2 taps at every size
+        else if (ctx->box_radius) p = RL_PATH_SPAN;
         // dense taps within 4 pixels of the anchor: the register-blocked
         // stencil beats span sums (every tap a register operand)
         else if (ctx->sq_k) p = RL_PATH_STENCIL;
@@ -645,13 +658,16 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
     return RL_OK;
 }
 
-// Disc path: two launches per iteration (forward + ratio, adjoint + update).
-// The adjoint half reads u only at its own pixels, so u and the mask are
-// updated in place in one working buffer; with thinning, tiles with no active
-// pixel skip both launches.
+// Block operations of the two-half kernels.
+enum HalfOp { OP_DISC = 0, OP_BOX = 1, OP_STENCIL = 2 };
+
+// Disc / box / register-stencil path: two launches per iteration (forward +
+// ratio, adjoint + update).  The adjoint half reads u only at its own pixels,
+// so u and the mask are updated in place in one working buffer; with
+// thinning, tiles with no active pixel skip both launches.
 rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, int W, int H,
-                   long long pitch, int K, const rl_thinning *thin, long long sp, int stencil_k) {
-    const int R = stencil_k ? stencil_k / 2 : ctx->disc_radius;
+                   long long pitch, int K, const rl_thinning *thin, long long sp, int op) {
+    const int R = op == OP_STENCIL ? ctx->sq_k / 2 : op == OP_BOX ? ctx->box_radius : ctx->disc_radius;
     const size_t es = elem_size(ctx->storage);
     const size_t plane = (size_t)sp * H;
     if (ctx->ubuf_bytes < plane * es) {
@@ -748,10 +764,11 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     };
     auto issue = [&](int k) -> rl_status {
         const IterArgs b = args_for(k);
-        cudaError_t e = stencil_k ? rl::launch_stencil(b, ctx->sq_taps.data(), stencil_k, ctx->storage,
-                                                       thin != nullptr, ctx->qplane, sp, ctx->stream)
-                                  : rl::launch_disc(b, ctx->storage, thin != nullptr, ctx->disc_radius,
-                                                    ctx->qplane, sp, ctx->stream);
+        cudaError_t e =
+            op == OP_STENCIL ? rl::launch_stencil(b, ctx->sq_taps.data(), ctx->sq_k, ctx->storage, thin != nullptr,
+                                                  ctx->qplane, sp, ctx->stream)
+            : op == OP_BOX   ? rl::launch_box(b, ctx->storage, thin != nullptr, R, ctx->qplane, sp, ctx->stream)
+                             : rl::launch_disc(b, ctx->storage, thin != nullptr, R, ctx->qplane, sp, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
         ctx->launches += 2;
         return RL_OK;
@@ -766,7 +783,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         const int G = thin ? thin->reset_period : 10;
         const int kend = thin ? K : K - 1;
         int kn = k;
-        st = run_segments(ctx, 1, kend, G >= 2 && G <= 64 ? G : 0, (thin ? 1 : 0) | stencil_k << 1, issue,
+        st = run_segments(ctx, 1, kend, G >= 2 && G <= 64 ? G : 0, (thin ? 1 : 0) | op << 1 | R << 3, issue,
                           args_for, &kn);
         if (st != RL_OK) return st;
         ctx->launches += (kn - k) * 2;
@@ -851,12 +868,17 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         CK(cudaMallocAsync(&ctx->ubuf[1], plane * es, ctx->stream), "rl_iterate: scratch u");
         ctx->ubuf_bytes = plane * es;
     }
-    const bool disc_fast = path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
-                           ctx->disc_radius <= rl::kDiscMaxRadius;
-    // centred odd square taps up to 9 x 9 take the register-blocked stencil
-    // taps within 4 pixels of the anchor take the register-blocked stencil
-    const int stencil_k = path == RL_PATH_STENCIL ? ctx->sq_k : 0;
-    if (disc_fast || stencil_k) {
+    // the register-blocked two-half kernels: the disc; a uniform centred
+    // square (box); taps within 4 pixels of the anchor (stencil)
+    int op = -1;
+    if (path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
+        ctx->disc_radius <= rl::kDiscMaxRadius)
+        op = OP_DISC;
+    else if (path == RL_PATH_SPAN && ctx->box_radius)
+        op = OP_BOX;
+    else if (path == RL_PATH_STENCIL && ctx->sq_k)
+        op = OP_STENCIL;
+    if (op >= 0) {
         if (ctx->q_px < plane) {
             sfree(ctx, ctx->qplane);
             ctx->qplane = nullptr;
@@ -865,7 +887,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             ctx->q_px = plane;
         }
         if (thin) CK(cudaMemsetAsync(ctx->qplane, 0, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
-        return run_disc(ctx, f, start, u_out, W, H, pitch, K, thin, sp, stencil_k);
+        return run_disc(ctx, f, start, u_out, W, H, pitch, K, thin, sp, op);
     }
 
     IterArgs a;

@@ -72,6 +72,19 @@ RL_DECLARE_DISC_R(9) RL_DECLARE_DISC_R(10) RL_DECLARE_DISC_R(11) RL_DECLARE_DISC
 RL_DECLARE_DISC_R(13) RL_DECLARE_DISC_R(14) RL_DECLARE_DISC_R(15) RL_DECLARE_DISC_R(16)
 #undef RL_DECLARE_DISC_R
 
+// Register-blocked uniform square box (2R + 1)^2, R = 1..16 (k_box_*.cu): the
+// disc's run sums with every run at half-width R.
+cudaError_t launch_box(const IterArgs &a, int storage, bool thin, int radius, float *qplane, long long q_pitch,
+                       cudaStream_t s);
+#define RL_DECLARE_BOX_R(R)                                                                  \
+    cudaError_t launch_box_r##R(const IterArgs &a, int storage, bool thin, float *qplane,    \
+                                long long q_pitch, cudaStream_t s);
+RL_DECLARE_BOX_R(1) RL_DECLARE_BOX_R(2) RL_DECLARE_BOX_R(3) RL_DECLARE_BOX_R(4)
+RL_DECLARE_BOX_R(5) RL_DECLARE_BOX_R(6) RL_DECLARE_BOX_R(7) RL_DECLARE_BOX_R(8)
+RL_DECLARE_BOX_R(9) RL_DECLARE_BOX_R(10) RL_DECLARE_BOX_R(11) RL_DECLARE_BOX_R(12)
+RL_DECLARE_BOX_R(13) RL_DECLARE_BOX_R(14) RL_DECLARE_BOX_R(15) RL_DECLARE_BOX_R(16)
+#undef RL_DECLARE_BOX_R
+
 // Exact-transpose band between the two halves (a.fold_ct set): A^T q on the
 // pixels within (fold_rx, fold_ry) of the border, from the full q plane.
 cudaError_t launch_fold_band(const IterArgs &a, const float *qplane, long long q_pitch, cudaStream_t s);

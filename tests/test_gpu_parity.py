@@ -109,9 +109,56 @@ def test_asymmetric_centred_square_taps(k, boundary):
     assert oracle.rel_linf(u, ref) <= 30 * 2.0 ** -9
 
 
+@pytest.mark.parametrize("boundary", ["mirror", "clamp"])
+@pytest.mark.parametrize("k", [3, 5, 9, 15, 23, 33])
+def test_uniform_square_box(k, boundary):
+    # A uniform centred odd square (Sec. 3, rectangular blur) takes the
+    # register-blocked box kernel (path 2): separable sums, every radius
+    # 1..16; 203 x 161 is ragged against the 64 x 64 tiles.
+    spec = synth.dense(np.ones((k, k)))
+    f32 = case(203, 161, spec, seed=synth.SEED_BASE + 53)
+    u, st = gpu_rl(spec, f32, 30, boundary=boundary)
+    assert st.path == 2
+    ref = oracle.rl(f32.astype(np.float64), oracle_psf(spec), 30, boundary=boundary).u
+    assert oracle.rel_linf(u, ref) <= TOL
+    # the generic stencil tiles compute the same convolution tap by tap
+    if k <= 15:
+        v, sv = gpu_rl(spec, f32, 30, path="stencil", boundary=boundary)
+        assert sv.path == 3
+        assert oracle.rel_linf(u, v) <= TOL
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_uniform_square_box_reduced_storage(storage):
+    # RL under a box PSF amplifies a perturbation of u by more than the
+    # factor one the general storage test assumes, so the bound here is
+    # measured on the oracle itself: its FP64 iterates with u rounded to the
+    # storage format after every iteration (what 16-bit storage does) drift
+    # from the unrounded ones by e; the GPU may differ from the unrounded
+    # oracle by 2 e (its FP32 arithmetic flips some of the rounding
+    # decisions).
+    K = 30
+    spec = synth.dense(np.ones((11, 11)))
+    f32 = case(150, 133, spec, seed=synth.SEED_BASE + 54)
+    dt = {"bf16": torch.bfloat16, "f16": torch.float16}[storage]
+    f_r = torch.from_numpy(f32).to(dt).float().numpy()
+    u, st = gpu_rl(spec, f_r, K, storage=storage)
+    assert st.path == 2
+    f64, psf = f_r.astype(np.float64), oracle_psf(spec)
+    ref = oracle.rl(f64, psf, K).u
+    rounded = f64
+    for _ in range(K):
+        rounded = oracle.rl(f64, psf, 1, u0=rounded).u
+        rounded = torch.from_numpy(rounded).to(dt).double().numpy()
+    e = oracle.rel_linf(rounded, ref)
+    assert e >= UNIT_ROUNDOFF[storage] / 2  # the rounding did happen
+    assert oracle.rel_linf(u, ref) <= 2 * e
+
+
 def test_uniform_rectangle_from_dense_taps_auto_path():
-    # within 4 pixels of the anchor: register-blocked stencil; wider: span sums
-    for shape, path in (((3, 5), 3), ((3, 11), 2), ((13, 1), 2)):
+    # uniform centred squares: the box kernel; other rectangles within 4
+    # pixels of the anchor: register-blocked stencil; wider: span sums
+    for shape, path in (((3, 5), 3), ((3, 11), 2), ((13, 1), 2), ((5, 5), 2), ((35, 35), 2)):
         spec = synth.dense(np.ones(shape))
         f32 = case(150, 90, spec)
         u, st = gpu_rl(spec, f32, 40)
@@ -320,7 +367,7 @@ def test_infinite_threshold_keeps_only_full_iterations():
 THIN_CASES = [(True, 1e-4, 1), (True, 1e-3, 1), (True, 1e-4, 10), (False, 0.01, 1),
               (False, 0.05, 10)]
 THIN_PATHS = [(synth.disc(4), "span"), (synth.disc(4), "stencil"), (synth.motion(15, 0), "runsum"),
-              (synth.motion(15, 1), "runsum")]
+              (synth.motion(15, 1), "runsum"), (synth.dense(np.ones((7, 7))), "span")]
 
 
 @pytest.mark.parametrize("relative,tau,q", THIN_CASES)

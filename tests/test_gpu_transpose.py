@@ -104,7 +104,11 @@ CASES = [
     Disc(5),
     # reaches 10 pixels from its anchor: the generic stencil tiles fold it
     Anchored(asym_taps((3, 11), 5), 10, 1, "dense3x11_anchor101"),
+    # uniform centred squares: the box kernel with the band fold
+    Anchored(np.ones((9, 9)), 4, 4, "box9"),
+    Anchored(np.ones((25, 25)), 12, 12, "box25"),
 ]
+BOX_CASES = ("box9", "box25")
 
 
 def gpu_run(spec, f32, iters, boundary, adjoint, thin=None, stats=False):
@@ -141,7 +145,7 @@ def test_transpose_matches_oracle(spec, boundary):
         # fold runs in the resident rows for motion PSFs, else in the stencil
         # tiles
         assert oracle.rel_linf(pf, ref) > 10 * TOL
-        assert st.path == {"motion": 1, "disc": 2}.get(spec.kind, 3)
+        assert st.path == (2 if spec.name in BOX_CASES else {"motion": 1, "disc": 2}.get(spec.kind, 3))
 
 
 @pytest.mark.parametrize("shape", [(9, 11), (6, 40), (40, 6), (13, 13)])
@@ -179,7 +183,8 @@ def test_symmetric_psf_under_mirror_is_unchanged():
         assert sa.path == sb.path
 
 
-@pytest.mark.parametrize("spec", [CASES[0], CASES[-1], Motion(6, 0), Motion(8, 1), Disc(4)], ids=lambda s: s.name)
+@pytest.mark.parametrize("spec", [CASES[0], CASES[10], Motion(6, 0), Motion(8, 1), Disc(4), CASES[-2]],
+                         ids=lambda s: s.name)
 @pytest.mark.parametrize("boundary", ["mirror", "clamp"])
 def test_transpose_thinned_replay(boundary, spec):
     # the oracle's used-pixel schedule replayed: same selective convolutions
