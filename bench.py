@@ -189,6 +189,9 @@ def run_case(args):
                                  synth.dense(np.eye(9)[::-1]))}
     # uniform centred squares (register-blocked box kernel)
     specs.update({f"box{k}": synth.dense(np.ones((k, k))) for k in (3, 9, 17, 33)})
+    # other uniform rectangles (register-blocked rectangle kernel)
+    specs.update({f"rect{h}x{w}": synth.dense(np.ones((h, w))) for h, w in ((3, 5), (9, 7), (9, 31), (31, 9),
+                                                                           (33, 31))})
     spec = specs[args.case]
     g = synth.latent_image(args.size, args.size, synth.SEED_BASE + 2)
     f32 = np.maximum(synth.blur(g, spec), 0.0).astype(np.float32)

@@ -73,15 +73,16 @@ typedef enum {
 
 typedef enum {
     RL_PATH_AUTO = 0,    /* motion -> RUNSUM, disc -> SPAN; dense -> STENCIL,
-                            except a uniform centred odd square up to 33 x 33
-                            (box, Sec. 3 rectangular blur) and uniform taps
-                            reaching more than 4 pixels from the anchor
-                            -> SPAN                                             */
+                            except -> SPAN: a uniform centred odd square up to
+                            33 x 33 (box, Sec. 3 rectangular blur), another
+                            uniform rectangle reaching 4..16 pixels from the
+                            anchor, and other uniform taps reaching more than
+                            4 pixels                                            */
     RL_PATH_RUNSUM = 1,  /* sliding-window box filter along x or y (motion only)  */
     RL_PATH_SPAN = 2,    /* per-row span sums of a uniform PSF (motion, disc,
                             or dense taps that are uniform with one contiguous
                             run per row); separable sliding sums for a uniform
-                            centred odd square up to 33 x 33                     */
+                            rectangle reaching up to 16 pixels from the anchor  */
     RL_PATH_STENCIL = 3  /* direct summation over the non-zero taps (any PSF)     */
 } rl_path;
 

@@ -250,11 +250,15 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
 
 // Block operations of the generic half-iteration kernel.  kR is the halo
 // radius, kUniform says whether the result still has to be scaled by the
-// uniform tap weight, Params travels in the kernel's parameter block.
+// uniform tap weight, Params travels in the kernel's parameter block.  An op
+// with kPrepass runs prepass() over the staged tile (all threads, then a
+// barrier) before the blocks, into kExtraFloats of shared memory after it.
 template <int R>
 struct DiscOp {
     static constexpr int kR = R;
     static constexpr bool kUniform = true;
+    static constexpr bool kPrepass = false;
+    static constexpr int kExtraFloats = 0;
     struct Params {};
     template <bool FWD>
     static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
@@ -330,11 +334,78 @@ template <int R>
 struct BoxOp {
     static constexpr int kR = R;
     static constexpr bool kUniform = true;
+    static constexpr bool kPrepass = false;
+    static constexpr int kExtraFloats = 0;
     struct Params {};
     template <bool FWD>
     static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
                                                  const Params &) {
         box_block<R>(tile, row0, bx, acc);  // symmetric: forward = adjoint
+    }
+};
+
+// Uniform rectangle of any size and anchor within the halo R (Sec. 3,
+// rectangular blur: separable sliding sums), given at run time as the tap
+// offsets [lox, hix] x [loy, hiy] about the anchor.  The prepass forms the
+// vertical sums V(r, c) of every staged column for the tile's rows, in a
+// separate plane; each block then slides the horizontal sums along V.  Both
+// passes cost O(1) per pixel whatever the rectangle's size.
+template <int R>
+struct RectOp {
+    static constexpr int kR = R;
+    static constexpr bool kUniform = true;
+    static constexpr bool kPrepass = true;
+    using G = Halo<R>;
+    // V row pitch: a multiple of 8, room for the column skew (one float per
+    // 32 columns) and the row skew (2 ((r >> 2) & 3)), which together keep the
+    // 32 lanes of a warp -- 8 columns 8 apart x 4 rows 4 apart -- on distinct
+    // banks
+    static constexpr int VP = (G::HP + G::HP / 32 + 7 + 7) / 8 * 8;
+    static constexpr int kExtraFloats = TY * VP;
+    struct Params { int lox, hix, loy, hiy; };
+    static __device__ __forceinline__ int vidx(int r, int c) { return r * VP + c + (c >> 5) + 2 * ((r >> 2) & 3); }
+    // staged-tile index of logical column c of staged row m (16-byte units swizzled)
+    static __device__ __forceinline__ int sidx(int m, int c) { return m * G::HP + (hunit(c >> 2) << 2) + (c & 3); }
+
+    // V(r, c) = sum over d in [dlo, dhi] of staged row r + R + d, column c;
+    // forward: v(p) = sum_t u(p - t), so d runs over -[loy, hiy]; adjoint:
+    // c(p) = sum_t q(p + t).  A column's sum slides down 16 rows, then
+    // restarts (bounded FP32 drift).
+    template <bool FWD>
+    static __device__ __forceinline__ void prepass(const float *tile, float *V, const Params &p) {
+        const int dlo = FWD ? -p.hiy : p.loy, dhi = FWD ? -p.loy : p.hiy;
+        constexpr int NG = TY / 16;
+        for (int it = threadIdx.x; it < G::HP * NG; it += 128) {
+            const int c = it % G::HP, r0 = it / G::HP * 16;
+            float s = 0.f;
+            for (int d = dlo; d <= dhi; ++d) s += tile[sidx(r0 + R + d, c)];
+            V[vidx(r0, c)] = s;
+#pragma unroll 5
+            for (int r = r0 + 1; r < r0 + 16; ++r) {
+                s += tile[sidx(r + R + dhi, c)] - tile[sidx(r - 1 + R + dlo, c)];
+                V[vidx(r, c)] = s;
+            }
+        }
+    }
+
+    template <bool FWD>
+    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
+                                                 const Params &p) {
+        const float *V = tile + G::NR * G::HP;
+        const int elo = FWD ? -p.hix : p.lox, ehi = FWD ? -p.lox : p.hix;
+        const int c0 = bx * SX + G::R4 + elo;  // V column of output 0's first term
+#pragma unroll
+        for (int i = 0; i < SY; ++i) {
+            const int r = row0 + i;
+            float s = 0.f;
+            for (int c = c0; c <= c0 + ehi - elo; ++c) s += V[vidx(r, c)];
+            acc[i][0] = s;
+#pragma unroll
+            for (int j = 1; j < SX; ++j) {
+                s += V[vidx(r, c0 + j + ehi - elo)] - V[vidx(r, c0 + j - 1)];
+                acc[i][j] = s;
+            }
+        }
     }
 };
 
@@ -345,6 +416,8 @@ template <int K>
 struct StencilOp {
     static constexpr int kR = K / 2;
     static constexpr bool kUniform = false;
+    static constexpr bool kPrepass = false;
+    static constexpr int kExtraFloats = 0;
     struct Params { float w[K * K]; };  // w[(ty + R) * K + (tx + R)] = h(tx, ty)
     template <bool FWD>
     static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
@@ -508,6 +581,10 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
                                         threadIdx.x);
     cp_async_wait_all();
     __syncthreads();
+    if constexpr (Op::kPrepass) {
+        Op::template prepass<FWD>(sm, sm + G::NR * G::HP, prm);
+        __syncthreads();
+    }
     // Natural block of this thread: warp w covers block rows 4w .. 4w + 3,
     // lane = 8 (x) x 4 (y) blocks, so the 8 lanes of a 16-byte load phase
     // share a block row.
@@ -656,7 +733,7 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                        long long q_pitch, cudaStream_t s) {
-    constexpr size_t smem = Halo<Op::kR>::bytes;
+    constexpr size_t smem = Halo<Op::kR>::bytes + Op::kExtraFloats * sizeof(float);
     cudaError_t e = ensure_smem<k_disc_half<T, THIN, Op, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
@@ -708,6 +785,16 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
     cudaError_t launch_box_r##R(const IterArgs &a, int storage, bool thin, float *qplane,    \
                                 long long q_pitch, cudaStream_t s) {                         \
         return disc::launch_op<disc::BoxOp<R>>(a, {}, storage, thin, qplane, q_pitch, s);   \
+    }                                                                                        \
+    }
+
+#define RL_RECT_TU(R)                                                                        \
+    namespace rl {                                                                           \
+    cudaError_t launch_rect_r##R(const IterArgs &a, int lox, int hix, int loy, int hiy,      \
+                                 int storage, bool thin, float *qplane, long long q_pitch,   \
+                                 cudaStream_t s) {                                           \
+        return disc::launch_op<disc::RectOp<R>>(a, {lox, hix, loy, hiy}, storage, thin,      \
+                                                qplane, q_pitch, s);                         \
     }                                                                                        \
     }
 

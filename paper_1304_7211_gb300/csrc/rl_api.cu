@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -38,6 +39,8 @@ struct rl_ctx {
     std::vector<float> sq_taps;          // taps embedded in a centred K x K square (K <= 9), or empty
     int sq_k = 0;
     int box_radius = 0;                  // uniform centred (2R + 1)^2 square, R <= 16, else 0
+    bool rect = false;                   // uniform rectangle of taps reaching <= 16 from the anchor
+    int rect_lox = 0, rect_hix = 0, rect_loy = 0, rect_hiy = 0;  // its tap offsets
     bool uniform = false;                // one contiguous run of equal taps per row
     bool axis_sym = false;               // h(tx, ty) = h(-tx, ty) = h(tx, -ty)
     std::vector<int2> spans;             // per row j: [lo, hi] offsets (lo > hi = empty)
@@ -439,6 +442,30 @@ rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
         for (int j = 0; j < kh && full; ++j) full = spans[j].x == -ax && spans[j].y == kw - 1 - ax;
         if (full) ctx->box_radius = kw / 2;
     }
+    // A uniform rectangle: the non-empty PSF rows are contiguous and share
+    // one span (register-blocked separable sums, any anchor).
+    ctx->rect = false;
+    if (uniform) {
+        int jlo = -1, jhi = -1;
+        bool same = true;
+        for (int j = 0; j < kh; ++j) {
+            if (spans[j].x > spans[j].y) continue;
+            if (jlo < 0) jlo = j;
+            else same = same && jhi == j - 1 && spans[j].x == spans[jlo].x && spans[j].y == spans[jlo].y;
+            jhi = j;
+        }
+        if (jlo >= 0 && same) {
+            const int lox = spans[jlo].x, hix = spans[jlo].y, loy = jlo - ay, hiy = jhi - ay;
+            const int reach = std::max(std::max(std::abs(lox), std::abs(hix)), std::max(std::abs(loy), std::abs(hiy)));
+            if (reach <= rl::kRectMaxReach) {
+                ctx->rect = true;
+                ctx->rect_lox = lox;
+                ctx->rect_hix = hix;
+                ctx->rect_loy = loy;
+                ctx->rect_hiy = hiy;
+            }
+        }
+    }
     ctx->spans = spans;
     ctx->weight = uniform ? (float)(common / sum) : 0.f;
     ctx->has_psf = true;
@@ -469,16 +496,19 @@ int choose_path(const rl_ctx *ctx, int W) {
     if (needs_fold(ctx)) {
         if (ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 && ctx->disc_radius <= rl::kDiscMaxRadius)
             return RL_PATH_SPAN;
-        if (ctx->box_radius) return RL_PATH_SPAN;
+        if (ctx->box_radius || (ctx->kind == RL_PSF_DENSE && ctx->rect)) return RL_PATH_SPAN;
         return RL_PATH_STENCIL;
     }
     int p = ctx->path_pref;
     if (p == RL_PATH_AUTO) {
         if (ctx->kind == RL_PSF_MOTION) p = RL_PATH_RUNSUM;
         else if (ctx->kind == RL_PSF_DISC) p = RL_PATH_SPAN;
-        // a uniform centred square: separable box sums beat the stencil's
-        // K^2 taps at every size
+        // a uniform centred square: the box kernel beats the stencil's taps
+        // at every size; another uniform rectangle: the rectangle kernel,
+        // except within 3 pixels of the anchor, where the register stencil
+        // (K <= 7) is faster than its shared-memory passes
         else if (ctx->box_radius) p = RL_PATH_SPAN;
+        else if (ctx->rect && !(ctx->sq_k && ctx->sq_k <= 7)) p = RL_PATH_SPAN;
         // dense taps within 4 pixels of the anchor: the register-blocked
         // stencil beats span sums (every tap a register operand)
         else if (ctx->sq_k) p = RL_PATH_STENCIL;
@@ -659,7 +689,7 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
 }
 
 // Block operations of the two-half kernels.
-enum HalfOp { OP_DISC = 0, OP_BOX = 1, OP_STENCIL = 2 };
+enum HalfOp { OP_DISC = 0, OP_BOX = 1, OP_STENCIL = 2, OP_RECT = 3 };
 
 // Disc / box / register-stencil path: two launches per iteration (forward +
 // ratio, adjoint + update).  The adjoint half reads u only at its own pixels,
@@ -667,7 +697,11 @@ enum HalfOp { OP_DISC = 0, OP_BOX = 1, OP_STENCIL = 2 };
 // thinning, tiles with no active pixel skip both launches.
 rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, int W, int H,
                    long long pitch, int K, const rl_thinning *thin, long long sp, int op) {
-    const int R = op == OP_STENCIL ? ctx->sq_k / 2 : op == OP_BOX ? ctx->box_radius : ctx->disc_radius;
+    const int R = op == OP_STENCIL ? ctx->sq_k / 2
+                  : op == OP_BOX   ? ctx->box_radius
+                  : op == OP_RECT  ? rl::rect_halo(std::max(std::max(std::abs(ctx->rect_lox), std::abs(ctx->rect_hix)),
+                                                            std::max(std::abs(ctx->rect_loy), std::abs(ctx->rect_hiy))))
+                                   : ctx->disc_radius;
     const size_t es = elem_size(ctx->storage);
     const size_t plane = (size_t)sp * H;
     if (ctx->ubuf_bytes < plane * es) {
@@ -768,6 +802,8 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
             op == OP_STENCIL ? rl::launch_stencil(b, ctx->sq_taps.data(), ctx->sq_k, ctx->storage, thin != nullptr,
                                                   ctx->qplane, sp, ctx->stream)
             : op == OP_BOX   ? rl::launch_box(b, ctx->storage, thin != nullptr, R, ctx->qplane, sp, ctx->stream)
+            : op == OP_RECT  ? rl::launch_rect(b, ctx->rect_lox, ctx->rect_hix, ctx->rect_loy, ctx->rect_hiy,
+                                               ctx->storage, thin != nullptr, ctx->qplane, sp, ctx->stream)
                              : rl::launch_disc(b, ctx->storage, thin != nullptr, R, ctx->qplane, sp, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: kernel launch");
         ctx->launches += 2;
@@ -869,13 +905,16 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         ctx->ubuf_bytes = plane * es;
     }
     // the register-blocked two-half kernels: the disc; a uniform centred
-    // square (box); taps within 4 pixels of the anchor (stencil)
+    // square (box); another uniform rectangle given as dense taps (rect);
+    // taps within 4 pixels of the anchor (stencil)
     int op = -1;
     if (path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
         ctx->disc_radius <= rl::kDiscMaxRadius)
         op = OP_DISC;
     else if (path == RL_PATH_SPAN && ctx->box_radius)
         op = OP_BOX;
+    else if (path == RL_PATH_SPAN && ctx->kind == RL_PSF_DENSE && ctx->rect)
+        op = OP_RECT;
     else if (path == RL_PATH_STENCIL && ctx->sq_k)
         op = OP_STENCIL;
     if (op >= 0) {

@@ -262,7 +262,8 @@ __device__ __forceinline__ void count_active(unsigned long long *ctr, bool use) 
 }
 
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in
-// maximum, once per kernel and device (the attribute persists in the context).
+// maximum less the kernel's static shared memory, once per kernel and device
+// (the attribute persists in the context).
 template <auto KERN>
 inline cudaError_t ensure_smem(size_t bytes) {
     static unsigned long long done = 0;  // bit per device ordinal (< 64)
@@ -275,8 +276,12 @@ inline cudaError_t ensure_smem(size_t bytes) {
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncAttributes fa = {};
+    e = cudaFuncGetAttributes(&fa, KERN);
+    if (e != cudaSuccess) return e;
+    const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (bytes > room) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
     if (e == cudaSuccess) __atomic_fetch_or(&done, bit, __ATOMIC_RELEASE);
     return e;
 }

@@ -85,6 +85,17 @@ RL_DECLARE_BOX_R(9) RL_DECLARE_BOX_R(10) RL_DECLARE_BOX_R(11) RL_DECLARE_BOX_R(1
 RL_DECLARE_BOX_R(13) RL_DECLARE_BOX_R(14) RL_DECLARE_BOX_R(15) RL_DECLARE_BOX_R(16)
 #undef RL_DECLARE_BOX_R
 
+// Register-blocked uniform rectangle [lox, hix] x [loy, hiy] (tap offsets
+// about the anchor, each within the halo R in {4, 8, 16}; k_rect.cu):
+// separable sliding sums through a shared-memory plane of vertical sums.
+constexpr int kRectMaxReach = 16;
+int rect_halo(int reach);  // the halo class for a reach, 0 if none
+cudaError_t launch_rect(const IterArgs &a, int lox, int hix, int loy, int hiy, int storage, bool thin,
+                        float *qplane, long long q_pitch, cudaStream_t s);
+cudaError_t launch_rect_r4(const IterArgs &, int, int, int, int, int, bool, float *, long long, cudaStream_t);
+cudaError_t launch_rect_r8(const IterArgs &, int, int, int, int, int, bool, float *, long long, cudaStream_t);
+cudaError_t launch_rect_r16(const IterArgs &, int, int, int, int, int, bool, float *, long long, cudaStream_t);
+
 // Exact-transpose band between the two halves (a.fold_ct set): A^T q on the
 // pixels within (fold_rx, fold_ry) of the border, from the full q plane.
 cudaError_t launch_fold_band(const IterArgs &a, const float *qplane, long long q_pitch, cudaStream_t s);

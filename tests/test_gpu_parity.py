@@ -128,8 +128,39 @@ def test_uniform_square_box(k, boundary):
         assert oracle.rel_linf(u, v) <= TOL
 
 
+def anchored(taps, ax, ay):
+    """Dense taps with an explicit anchor, as the PSF descriptor takes them."""
+    t = np.asarray(taps, np.float64)
+    return type("S", (), dict(kind="dense", taps=tuple(t.reshape(-1)), kw=t.shape[1], kh=t.shape[0],
+                              anchor_x=ax, anchor_y=ay, axis=0, length=0, radius=0,
+                              name=f"rect{t.shape[0]}x{t.shape[1]}_a{ax}_{ay}", t=t))()
+
+
+# (rows, cols, anchor x, anchor y): centred and off-centre, even and odd,
+# thin in either axis, reaching 1..16 pixels from the anchor
+RECTS = [(3, 5, 2, 1), (9, 31, 15, 4), (31, 9, 4, 15), (1, 17, 8, 0), (17, 1, 0, 8), (8, 8, 4, 4),
+         (6, 11, 0, 0), (2, 33, 16, 1), (12, 4, 3, 11), (21, 15, 7, 10)]
+
+
+@pytest.mark.parametrize("boundary", ["mirror", "clamp"])
+@pytest.mark.parametrize("rect", RECTS, ids=lambda r: "x".join(map(str, r)))
+def test_uniform_rectangle(rect, boundary):
+    # A uniform rectangle of any anchor within 16 pixels (Sec. 3,
+    # rectangular blur) takes the register-blocked rectangle kernel on the
+    # span path: vertical sums in shared memory, horizontal sums slid along
+    # them.
+    kh, kw, ax, ay = rect
+    spec = anchored(np.ones((kh, kw)), ax, ay)
+    f32 = case(203, 161, synth.disc(2), seed=synth.SEED_BASE + 55)
+    u, st = gpu_rl(spec, f32, 30, path="span", boundary=boundary)
+    assert st.path == 2
+    ref = oracle.rl(f32.astype(np.float64), oracle.psf_dense(spec.t, ax, ay), 30, boundary=boundary).u
+    assert oracle.rel_linf(u, ref) <= TOL
+
+
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-def test_uniform_square_box_reduced_storage(storage):
+@pytest.mark.parametrize("shape", [(11, 11), (7, 15)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_uniform_box_and_rectangle_reduced_storage(storage, shape):
     # RL under a box PSF amplifies a perturbation of u by more than the
     # factor one the general storage test assumes, so the bound here is
     # measured on the oracle itself: its FP64 iterates with u rounded to the
@@ -138,7 +169,7 @@ def test_uniform_square_box_reduced_storage(storage):
     # oracle by 2 e (its FP32 arithmetic flips some of the rounding
     # decisions).
     K = 30
-    spec = synth.dense(np.ones((11, 11)))
+    spec = synth.dense(np.ones(shape))
     f32 = case(150, 133, spec, seed=synth.SEED_BASE + 54)
     dt = {"bf16": torch.bfloat16, "f16": torch.float16}[storage]
     f_r = torch.from_numpy(f32).to(dt).float().numpy()
@@ -156,9 +187,11 @@ def test_uniform_square_box_reduced_storage(storage):
 
 
 def test_uniform_rectangle_from_dense_taps_auto_path():
-    # uniform centred squares: the box kernel; other rectangles within 4
-    # pixels of the anchor: register-blocked stencil; wider: span sums
-    for shape, path in (((3, 5), 3), ((3, 11), 2), ((13, 1), 2), ((5, 5), 2), ((35, 35), 2)):
+    # uniform centred squares: the box kernel; other uniform rectangles
+    # within 3 pixels of the anchor: the register stencil; up to 16: the
+    # rectangle kernel; beyond: the span tiles
+    for shape, path in (((3, 5), 3), ((3, 11), 2), ((13, 1), 2), ((5, 5), 2), ((35, 35), 2), ((3, 41), 2),
+                        ((9, 7), 2)):
         spec = synth.dense(np.ones(shape))
         f32 = case(150, 90, spec)
         u, st = gpu_rl(spec, f32, 40)
@@ -367,7 +400,8 @@ def test_infinite_threshold_keeps_only_full_iterations():
 THIN_CASES = [(True, 1e-4, 1), (True, 1e-3, 1), (True, 1e-4, 10), (False, 0.01, 1),
               (False, 0.05, 10)]
 THIN_PATHS = [(synth.disc(4), "span"), (synth.disc(4), "stencil"), (synth.motion(15, 0), "runsum"),
-              (synth.motion(15, 1), "runsum"), (synth.dense(np.ones((7, 7))), "span")]
+              (synth.motion(15, 1), "runsum"), (synth.dense(np.ones((7, 7))), "span"),
+              (synth.dense(np.ones((5, 13))), "span")]
 
 
 @pytest.mark.parametrize("relative,tau,q", THIN_CASES)
@@ -395,8 +429,11 @@ def test_thinned_free_running_masks(spec, path, relative, tau, q):
     """GPU decisions (FP32) against the oracle's (FP64): the final masks are
     compared by the count of disagreeing pixels, the active counts by their
     relative difference.  A disagreement needs a change within rounding of
-    the threshold, so both stay tiny; the image difference they cause is
-    reported."""
+    the threshold, so both stay tiny.  The image difference those flips cause
+    depends on the PSF, so its bound is measured on the oracle: its own
+    iterates with tau moved by 1e-3 relative (the FP32 rounding of the Eq. 4
+    statistic near tau = 1e-4) differ by `spread`; the GPU may differ by
+    twice that, and never needs to be closer than 1e-2."""
     from paper_1304_7211_gb300 import rl
     K = 34
     f32 = case(170, 150, spec, seed=synth.SEED_BASE + 52)
@@ -413,7 +450,9 @@ def test_thinned_free_running_masks(spec, path, relative, tau, q):
           f"act_rel={act_rel:.2e} image_rel_linf={err:.2e}")
     assert dis <= 0.005 * mask.size
     assert act_rel <= 0.005
-    assert err <= 1e-2
+    spread = max(oracle.rel_linf(oracle.rl(f64, oracle_psf(spec), K, threshold=tau * (1 + d), relative=relative,
+                                           update_period=q).u, res.u) for d in (1e-3, -1e-3))
+    assert err <= max(1e-2, 2 * spread)
 
 
 # ---- running sum: whole rows resident vs one launch per iteration -------------

@@ -107,8 +107,24 @@ CASES = [
     # uniform centred squares: the box kernel with the band fold
     Anchored(np.ones((9, 9)), 4, 4, "box9"),
     Anchored(np.ones((25, 25)), 12, 12, "box25"),
+    # uniform rectangles off their centre: the rectangle kernel with the fold
+    Anchored(np.ones((6, 11)), 0, 0, "rect6x11_corner"),
+    Anchored(np.ones((3, 21)), 15, 1, "rect3x21_a15"),
 ]
-BOX_CASES = ("box9", "box25")
+
+
+def uniform_rectangle(spec):
+    """Equal taps filling a rectangle reaching <= 16 pixels from the anchor:
+    the library runs those on the box / rectangle kernels (path 2)."""
+    t = spec.t
+    if spec.kind != "dense":
+        return False
+    ys, xs = np.nonzero(t)
+    if len(ys) != (np.ptp(ys) + 1) * (np.ptp(xs) + 1) or not np.all(t[ys, xs] == t[ys[0], xs[0]]):
+        return False
+    reach = max(abs(xs.min() - spec.anchor_x), abs(xs.max() - spec.anchor_x),
+                abs(ys.min() - spec.anchor_y), abs(ys.max() - spec.anchor_y))
+    return reach <= 16
 
 
 def gpu_run(spec, f32, iters, boundary, adjoint, thin=None, stats=False):
@@ -142,10 +158,11 @@ def test_transpose_matches_oracle(spec, boundary):
         assert st.path != 3 or spec.kind == "dense"
     else:
         # not the pad-flip iterate (the test would be vacuous otherwise); the
-        # fold runs in the resident rows for motion PSFs, else in the stencil
-        # tiles
+        # fold runs in the resident rows for motion PSFs, on the two-half
+        # kernels for the disc and uniform rectangles, else in the stencil
+        # kernels
         assert oracle.rel_linf(pf, ref) > 10 * TOL
-        assert st.path == (2 if spec.name in BOX_CASES else {"motion": 1, "disc": 2}.get(spec.kind, 3))
+        assert st.path == (2 if uniform_rectangle(spec) else {"motion": 1, "disc": 2}.get(spec.kind, 3))
 
 
 @pytest.mark.parametrize("shape", [(9, 11), (6, 40), (40, 6), (13, 13)])
@@ -183,7 +200,7 @@ def test_symmetric_psf_under_mirror_is_unchanged():
         assert sa.path == sb.path
 
 
-@pytest.mark.parametrize("spec", [CASES[0], CASES[10], Motion(6, 0), Motion(8, 1), Disc(4), CASES[-2]],
+@pytest.mark.parametrize("spec", [CASES[0], CASES[10], Motion(6, 0), Motion(8, 1), Disc(4), CASES[11], CASES[13]],
                          ids=lambda s: s.name)
 @pytest.mark.parametrize("boundary", ["mirror", "clamp"])
 def test_transpose_thinned_replay(boundary, spec):
