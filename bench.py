@@ -262,6 +262,57 @@ def batch_run(local, n_images=64, slots=32):
             "timing": "host wall clock around submit..sync, inputs resident"}
 
 
+def tiles_run(local, n_images=64, slots=32):
+    """Batched (request, tile) workload: 64 frames under one disc r = 8 PSF,
+    sides log-uniform in [128, 512], 50..150 iterations each, as one
+    rl_iterate_tiles call (one launch pair per iteration over every frame's
+    tiles) vs rl_batch on 32 streams vs one solve at a time.  Returns a dict."""
+    import numpy as np
+    import torch
+    from paper_1304_7211_gb300 import rl, synth
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(synth.SEED_BASE + 90)
+    spec = synth.disc(8)
+    jobs = []
+    for j in range(n_images):
+        w, h = (int(round(np.exp(rng.uniform(np.log(128), np.log(512))))) for _ in range(2))
+        its = int(rng.integers(50, 151))
+        c = synth.make_case(w, h, spec, 0, "poisson", synth.SEED_BASE + 900 + j)
+        f = torch.from_numpy(c.f.astype(np.float32)).to(dev)
+        jobs.append((f, torch.empty_like(f), its, w, h))
+    px_it = float(sum(w * h * its for (_, _, its, w, h) in jobs))
+    ctx = rl.Deconvolver(spec, device=local)
+
+    def tiles():
+        rl.rl_iterate_tiles(ctx.ctx, [(f, None, u, w, h, w, its) for (f, u, its, w, h) in jobs])
+
+    def streams():
+        with rl.Batch(slots, device=local) as b:
+            for f, u, its, w, h in jobs:
+                b.submit(spec, f, u, its, w, h)
+            b.sync()
+
+    def sequential():
+        for f, u, its, w, h in jobs:
+            rl.rl_iterate(ctx.ctx, f, None, u, w, h, w, its)
+
+    ts = {}
+    for name, fn in (("tiles", tiles), ("streams", streams), ("sequential", sequential)):
+        fn()  # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize(dev)
+        ts[name] = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": f"{n_images} frames, one disc r8 PSF, sides log-uniform [128,512], 50-150 it; fp32",
+            "px_it": px_it, "unit": UNIT, "value": px_it / ts["tiles"] / 1e6,
+            "streams_value": px_it / ts["streams"] / 1e6, "sequential_value": px_it / ts["sequential"] / 1e6,
+            "tiles_ms": 1e3 * ts["tiles"], "streams_ms": 1e3 * ts["streams"],
+            "sequential_ms": 1e3 * ts["sequential"], "slots": slots,
+            "timing": "host wall clock around the call(s)..sync, inputs resident"}
+
+
 def serve_run(local, n=200, rate=100.0, slots=16):
     """Served workload: a Poisson-arrival trace (rate req/s), sides
     log-uniform in [256, 4096], PSF as in the batched workload, 50..500
@@ -517,6 +568,7 @@ def main():
             "roofline": roof, "clocks": clk}
     if not args.no_batch:
         line["batch"] = batch_run(local)
+        line["batch_tiles"] = tiles_run(local)
     if not args.no_serve:
         line["serve"] = serve_run(local, n=args.serve_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -283,6 +283,29 @@ rl_status rl_batch_destroy(rl_batch *b);
 /* Message of the last failure on b. */
 const char *rl_batch_last_error(const rl_batch *b);
 
+/*
+ * Batched (request, tile) form of the disc and box kernels (Eq. 3 per job;
+ * Sec. 3 defocus disc and rectangular box blur): n jobs that share ctx's PSF
+ * run as one forward and one adjoint launch per iteration over the 64 x 64
+ * tiles of every job still iterating, so many small images fill the GPU
+ * that one image alone would leave mostly idle.  A job leaves the work list
+ * when its own iteration count ends; each job's result is the image that
+ * rl_iterate gives for it alone.
+ *   ctx: its PSF must take the disc or box kernel (RL_PSF_DISC of radius
+ *       1..16, or dense taps forming a uniform centred odd square up to
+ *       33 x 33); FP32 storage; no exact-transpose band (clamp with
+ *       RL_FLAG_ADJOINT_TRANSPOSE).
+ *   jobs[j]: f, u0 (NULL = f), u_out device pointers, caller-owned, valid
+ *       until the work is done; u_out may alias u0 but not f; W, H, pitch
+ *       (elements), iterations.  psf is ignored (ctx's PSF applies); thin,
+ *       f_host and u_host must be NULL.
+ * Enqueued on ctx's stream (as rl_iterate); the library's scratch, one u and
+ * one q plane per job, is allocated and released in stream order.
+ * Errors: RL_ERR_INVALID_ARG, RL_ERR_STATE (no PSF), RL_ERR_UNSUPPORTED (PSF,
+ * storage, band, thinning or host buffers), RL_ERR_CUDA, RL_ERR_OOM.
+ */
+rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n);
+
 /* Library version string, e.g. "rl-gb300 0.1 sm_103a". */
 const char *rl_version(void);
 

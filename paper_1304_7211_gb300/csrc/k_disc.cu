@@ -31,6 +31,22 @@ cudaError_t launch_box(const IterArgs &a, int storage, bool thin, int radius, fl
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_tiles(int op, int radius, const TileJob *jobs, const int2 *items, int n_items, int phase,
+                         cudaStream_t s) {
+    switch (radius) {
+#define RL_TILES_CASE(R)                                                                    \
+    case R:                                                                                 \
+        return op == 0 ? launch_disc_tiles_r##R(jobs, items, n_items, phase, s)             \
+                       : launch_box_tiles_r##R(jobs, items, n_items, phase, s);
+    RL_TILES_CASE(1) RL_TILES_CASE(2) RL_TILES_CASE(3) RL_TILES_CASE(4) RL_TILES_CASE(5)
+    RL_TILES_CASE(6) RL_TILES_CASE(7) RL_TILES_CASE(8) RL_TILES_CASE(9) RL_TILES_CASE(10)
+    RL_TILES_CASE(11) RL_TILES_CASE(12) RL_TILES_CASE(13) RL_TILES_CASE(14) RL_TILES_CASE(15)
+    RL_TILES_CASE(16)
+#undef RL_TILES_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_stencil(const IterArgs &a, const float *taps, int K, int storage, bool thin,
                            float *qplane, long long q_pitch, cudaStream_t s) {
     switch (K) {

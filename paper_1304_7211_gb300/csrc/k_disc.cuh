@@ -553,25 +553,21 @@ __device__ __forceinline__ void st_mask8(uint8_t *p, int n, unsigned long long v
 template <int R, bool THIN>
 constexpr int min_blocks() { return R > 8 ? 4 : THIN || R == 1 ? 5 : 7; }
 
+// One 64 x 64 output tile (tbx, tby) of a half-iteration, run by the whole
+// CTA; the kernels below call it once per CTA.
 template <typename T, bool THIN, typename Op, bool FWD>
-__global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(IterArgs a, const __grid_constant__ typename Op::Params prm,
-                                                      float *qplane, long long q_pitch) {
+__device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::Params &prm, float *qplane,
+                                          long long q_pitch, int tbx, int tby) {
     constexpr int R = Op::kR;
     using G = Halo<R>;
     extern __shared__ float sm[];
-    // Programmatic dependent launch: this grid may start while the previous
-    // kernel of the stream drains; every read of its output (u, q, the tile
-    // flags) comes after this wait, and the next grid may launch as soon as
-    // every CTA of this one has started.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" :::);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = tbx * TX, y0 = tby * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
     bool tile_any = false;  // a pixel of this thread's blocks stays active
     // Selective convolution at tile granularity: a tile none of whose pixels
     // is active does nothing (u stays, q keeps the stale ratios).
-    int *tflag = (THIN && a.tile_flags) ? a.tile_flags + blockIdx.y * a.tiles_x + blockIdx.x : nullptr;
+    int *tflag = (THIN && a.tile_flags) ? a.tile_flags + tby * a.tiles_x + tbx : nullptr;
     if (tflag && !a.full && *tflag == 0) return;
     if (FWD)
         stage_halo<T, G::NR, G::NU>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
@@ -730,6 +726,36 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>()) k_disc_half(I
     }
 }
 
+template <typename T, bool THIN, typename Op, bool FWD>
+__global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>())
+    k_disc_half(const __grid_constant__ IterArgs a, const __grid_constant__ typename Op::Params prm, float *qplane,
+                long long q_pitch) {
+    // Programmatic dependent launch: this grid may start while the previous
+    // kernel of the stream drains; every read of its output (u, q, the tile
+    // flags) comes after this wait, and the next grid may launch as soon as
+    // every CTA of this one has started.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+    half_tile<T, THIN, Op, FWD>(a, prm, qplane, q_pitch, blockIdx.x, blockIdx.y);
+}
+
+// Batched (request, tile) form: CTA b runs tile items[b].y of job items[b].x,
+// with the job's arguments for the first iteration (phase 0) or the later
+// ones (phase 1).  Jobs of one launch share the block operation; FP32
+// storage, no thinning.
+template <typename Op, bool FWD>
+__global__ void __launch_bounds__(128, min_blocks<Op::kR, false>())
+    k_disc_half_tiles(const TileJob *jobs, const int2 *items, int phase,
+                      const __grid_constant__ typename Op::Params prm) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+    const int2 it = items[blockIdx.x];
+    const TileJob &job = jobs[it.x];
+    const IterArgs &a = job.a[phase];
+    const int tiles_x = (a.W + TX - 1) / TX;
+    half_tile<float, false, Op, FWD>(a, prm, job.qplane, job.q_pitch, it.y % tiles_x, it.y / tiles_x);
+}
+
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                        long long q_pitch, cudaStream_t s) {
@@ -750,6 +776,30 @@ cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float 
     e = cudaLaunchKernelEx(&cfg, k_disc_half<T, THIN, Op, true>, a, prm, qplane, q_pitch);
     if (e == cudaSuccess && a.fold_ct) e = launch_fold_band(a, qplane, q_pitch, s);
     if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_disc_half<T, THIN, Op, false>, a, prm, qplane, q_pitch);
+    return e;
+}
+
+// One forward and one adjoint launch of the batched form over n_items items.
+template <typename Op>
+cudaError_t launch_op_tiles(const TileJob *jobs, const int2 *items, int n_items, int phase,
+                            const typename Op::Params &prm, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    constexpr size_t smem = Halo<Op::kR>::bytes + Op::kExtraFloats * sizeof(float);
+    cudaError_t e = ensure_smem<k_disc_half_tiles<Op, true>>(smem);
+    if (e == cudaSuccess) e = ensure_smem<k_disc_half_tiles<Op, false>>(smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_items);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_disc_half_tiles<Op, true>, jobs, items, phase, prm);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_disc_half_tiles<Op, false>, jobs, items, phase, prm);
     return e;
 }
 
@@ -778,6 +828,10 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
                                  long long q_pitch, cudaStream_t s) {                        \
         return disc::launch_op<disc::DiscOp<R>>(a, {}, storage, thin, qplane, q_pitch, s);  \
     }                                                                                        \
+    cudaError_t launch_disc_tiles_r##R(const TileJob *jobs, const int2 *items, int n_items,  \
+                                       int phase, cudaStream_t s) {                          \
+        return disc::launch_op_tiles<disc::DiscOp<R>>(jobs, items, n_items, phase, {}, s);   \
+    }                                                                                        \
     }
 
 #define RL_BOX_TU(R)                                                                         \
@@ -785,6 +839,10 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
     cudaError_t launch_box_r##R(const IterArgs &a, int storage, bool thin, float *qplane,    \
                                 long long q_pitch, cudaStream_t s) {                         \
         return disc::launch_op<disc::BoxOp<R>>(a, {}, storage, thin, qplane, q_pitch, s);   \
+    }                                                                                        \
+    cudaError_t launch_box_tiles_r##R(const TileJob *jobs, const int2 *items, int n_items,   \
+                                      int phase, cudaStream_t s) {                           \
+        return disc::launch_op_tiles<disc::BoxOp<R>>(jobs, items, n_items, phase, {}, s);    \
     }                                                                                        \
     }
 

@@ -1156,6 +1156,153 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
     return RL_OK;
 }
 
+extern "C" rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n) {
+    if (!ctx) return RL_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !jobs)) return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate_tiles: need n >= 0 and jobs");
+    if (!ctx->has_psf) return fail(ctx, RL_ERR_STATE, "rl_iterate_tiles: no PSF set");
+    if (ctx->storage != RL_STORAGE_F32)
+        return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate_tiles: FP32 storage only");
+    if (needs_fold(ctx))
+        return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate_tiles: no exact-transpose band in the batched form");
+    int op = -1, R = 0;
+    if (ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 && ctx->disc_radius <= rl::kDiscMaxRadius) {
+        op = 0;
+        R = ctx->disc_radius;
+    } else if (ctx->box_radius) {
+        op = 1;
+        R = ctx->box_radius;
+    } else {
+        return fail(ctx, RL_ERR_UNSUPPORTED,
+                    "rl_iterate_tiles: the PSF must take the disc or box kernel (disc radius 1..16, or a "
+                    "uniform centred odd square up to 33 x 33)");
+    }
+    for (int j = 0; j < n; ++j) {
+        const rl_job &jb = jobs[j];
+        if (!jb.f || !jb.u_out || jb.u_out == jb.f || jb.W < 1 || jb.H < 1 || jb.pitch < jb.W ||
+            jb.iterations < 0)
+            return fail(ctx, RL_ERR_INVALID_ARG,
+                        "rl_iterate_tiles: each job needs f, u_out (not aliasing f), W, H >= 1, pitch >= W, "
+                        "iterations >= 0");
+        if (jb.thin || jb.f_host || jb.u_host)
+            return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate_tiles: no thinning or host buffers in the batched form");
+        if (R >= jb.W || R >= jb.H)
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate_tiles: PSF extent must be smaller than the image");
+        if (!is_device_ptr(jb.f) || !is_device_ptr(jb.u_out) || (jb.u0 && !is_device_ptr(jb.u0)))
+            return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate_tiles: f, u0 and u_out must be device pointers");
+    }
+    if (n == 0) return RL_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    struct Restore {
+        int d, p;
+        ~Restore() { if (d != p) cudaSetDevice(p); }
+    } restore{ctx->device, prev};
+    // default-stream contexts run on the internal stream, fenced (as rl_iterate)
+    struct Fence {
+        rl_ctx *c;
+        cudaStream_t user;
+        ~Fence() {
+            if (!c) return;
+            cudaEventRecord(c->ev_out, c->own);
+            cudaStreamWaitEvent(user, c->ev_out, 0);
+            c->stream = user;
+        }
+    } fence{nullptr, ctx->stream};
+    if (ctx->own) {
+        CK(cudaEventRecord(ctx->ev_in, ctx->stream), "rl_iterate_tiles: stream fence");
+        CK(cudaStreamWaitEvent(ctx->own, ctx->ev_in, 0), "rl_iterate_tiles: stream fence");
+        ctx->stream = ctx->own;
+        fence.c = ctx;
+    }
+    // Jobs by iteration count, descending: the jobs still iterating at
+    // iteration k are a prefix, and so are their tiles in the work list.
+    std::vector<int> ord(n);
+    for (int j = 0; j < n; ++j) ord[j] = j;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int x, int y) { return jobs[x].iterations > jobs[y].iterations; });
+    std::vector<long long> sp(n);
+    size_t plane_bytes = 0;
+    for (int j = 0; j < n; ++j) {
+        const rl_job &jb = jobs[ord[j]];
+        sp[j] = ((long long)jb.W + 63) / 64 * 64;
+        plane_bytes += (size_t)sp[j] * jb.H * sizeof(float) * 2;  // u and q
+    }
+    std::vector<rl::TileJob> tj(n);
+    std::vector<int2> items;
+    std::vector<long long> prefix(n + 1, 0);
+    for (int j = 0; j < n; ++j) {
+        const rl_job &jb = jobs[ord[j]];
+        const int tiles = ((jb.W + 63) / 64) * ((jb.H + 63) / 64);
+        for (int t = 0; t < (jb.iterations > 0 ? tiles : 0); ++t) items.push_back(make_int2(j, t));
+        prefix[j + 1] = (long long)items.size();
+    }
+    const size_t jobs_bytes = (n * sizeof(rl::TileJob) + 255) / 256 * 256;
+    const size_t items_bytes = std::max<size_t>(items.size(), 1) * sizeof(int2);
+    char *scratch = nullptr;
+    CK(cudaMallocAsync((void **)&scratch, plane_bytes + jobs_bytes + items_bytes, ctx->stream),
+       "rl_iterate_tiles: scratch");
+    struct Free {
+        char *p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } release{scratch, ctx->stream};
+    char *cur = scratch + jobs_bytes + items_bytes;
+    for (int j = 0; j < n; ++j) {
+        const rl_job &jb = jobs[ord[j]];
+        float *work = (float *)cur;
+        cur += (size_t)sp[j] * jb.H * sizeof(float);
+        float *q = (float *)cur;
+        cur += (size_t)sp[j] * jb.H * sizeof(float);
+        IterArgs a;
+        memset(&a, 0, sizeof a);
+        a.f = jb.f;
+        a.W = jb.W;
+        a.H = jb.H;
+        a.f_pitch = jb.pitch;
+        a.clamp = ctx->boundary == RL_BOUNDARY_CLAMP;
+        a.ax = a.bx = a.ay = a.by = R;
+        a.weight = ctx->weight;
+        a.m_pitch = a.mi_pitch = sp[j];
+        a.u_out = work;
+        a.out_pitch = sp[j];
+        tj[j].a[0] = a;
+        tj[j].a[0].u_in = jb.u0 ? jb.u0 : jb.f;  // first iteration reads the start image
+        tj[j].a[0].in_pitch = jb.pitch;
+        tj[j].a[1] = a;
+        tj[j].a[1].u_in = work;  // later ones update the work plane in place
+        tj[j].a[1].in_pitch = sp[j];
+        tj[j].qplane = q;
+        tj[j].q_pitch = sp[j];
+    }
+    auto *djobs = (rl::TileJob *)scratch;
+    auto *ditems = (int2 *)(scratch + jobs_bytes);
+    CK(cudaMemcpyAsync(djobs, tj.data(), n * sizeof(rl::TileJob), cudaMemcpyHostToDevice, ctx->stream),
+       "rl_iterate_tiles: job table");
+    if (!items.empty())
+        CK(cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream),
+           "rl_iterate_tiles: work list");
+    const int kmax = jobs[ord[0]].iterations;
+    int active = n;
+    for (int k = 0; k < kmax; ++k) {
+        while (active > 0 && jobs[ord[active - 1]].iterations <= k) --active;
+        CK(rl::launch_tiles(op, R, djobs, ditems, (int)prefix[active], k == 0 ? 0 : 1, ctx->stream),
+           "rl_iterate_tiles: kernel launch");
+    }
+    for (int j = 0; j < n; ++j) {
+        const rl_job &jb = jobs[ord[j]];
+        const void *src = jb.iterations > 0 ? (const void *)tj[j].a[1].u_in : (jb.u0 ? jb.u0 : jb.f);
+        const long long spitch = jb.iterations > 0 ? sp[j] : jb.pitch;
+        if (src != jb.u_out)
+            CK(cudaMemcpy2DAsync(jb.u_out, jb.pitch * sizeof(float), src, spitch * sizeof(float), jb.W * sizeof(float),
+                                 jb.H, cudaMemcpyDeviceToDevice, ctx->stream),
+               "rl_iterate_tiles: copy out");
+    }
+    CK(cudaGetLastError(), "rl_iterate_tiles");
+    ctx->err.clear();
+    return RL_OK;
+}
+
 extern "C" rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch) {
     if (!ctx) return RL_ERR_INVALID_ARG;
     if (!dst) return fail(ctx, RL_ERR_INVALID_ARG, "rl_get_mask: dst is NULL");

@@ -72,6 +72,28 @@ RL_DECLARE_DISC_R(9) RL_DECLARE_DISC_R(10) RL_DECLARE_DISC_R(11) RL_DECLARE_DISC
 RL_DECLARE_DISC_R(13) RL_DECLARE_DISC_R(14) RL_DECLARE_DISC_R(15) RL_DECLARE_DISC_R(16)
 #undef RL_DECLARE_DISC_R
 
+// Batched (request, tile) form of the disc and box halves: one job's
+// arguments for its first iteration (a[0]) and the later ones (a[1]), with
+// its q plane.  A launch pair runs one iteration of every listed item
+// (int2: job, tile index in row-major tile order).  FP32 storage, no
+// thinning, no transpose band.
+struct TileJob {
+    IterArgs a[2];
+    float *qplane;
+    long long q_pitch;
+};
+// op 0 = disc, 1 = box; radius 1..16
+cudaError_t launch_tiles(int op, int radius, const TileJob *jobs, const int2 *items, int n_items, int phase,
+                         cudaStream_t s);
+#define RL_DECLARE_TILES_R(R)                                                                 \
+    cudaError_t launch_disc_tiles_r##R(const TileJob *, const int2 *, int, int, cudaStream_t); \
+    cudaError_t launch_box_tiles_r##R(const TileJob *, const int2 *, int, int, cudaStream_t);
+RL_DECLARE_TILES_R(1) RL_DECLARE_TILES_R(2) RL_DECLARE_TILES_R(3) RL_DECLARE_TILES_R(4)
+RL_DECLARE_TILES_R(5) RL_DECLARE_TILES_R(6) RL_DECLARE_TILES_R(7) RL_DECLARE_TILES_R(8)
+RL_DECLARE_TILES_R(9) RL_DECLARE_TILES_R(10) RL_DECLARE_TILES_R(11) RL_DECLARE_TILES_R(12)
+RL_DECLARE_TILES_R(13) RL_DECLARE_TILES_R(14) RL_DECLARE_TILES_R(15) RL_DECLARE_TILES_R(16)
+#undef RL_DECLARE_TILES_R
+
 // Register-blocked uniform square box (2R + 1)^2, R = 1..16 (k_box_*.cu): the
 // disc's run sums with every run at half-width R.
 cudaError_t launch_box(const IterArgs &a, int storage, bool thin, int radius, float *qplane, long long q_pitch,

@@ -87,7 +87,7 @@ _lib = None
 EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error", "rl_version",
            "rl_get_mask", "rl_motion_x_noalloc", "rl_batch_create", "rl_batch_submit",
            "rl_batch_query", "rl_batch_wait", "rl_batch_sync", "rl_batch_destroy",
-           "rl_batch_last_error")
+           "rl_batch_last_error", "rl_iterate_tiles")
 RL_NOALLOC_MAX_PIXELS = 4194304
 
 
@@ -130,6 +130,8 @@ def load() -> ctypes.CDLL:
     lib.rl_batch_destroy.argtypes = [P]
     lib.rl_batch_last_error.restype = ctypes.c_char_p
     lib.rl_batch_last_error.argtypes = [P]
+    lib.rl_iterate_tiles.restype = ctypes.c_int
+    lib.rl_iterate_tiles.argtypes = [P, ctypes.POINTER(rl_job), ctypes.c_int]
     lib.rl_motion_x_noalloc.restype = ctypes.c_int
     lib.rl_motion_x_noalloc.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
@@ -209,6 +211,18 @@ def rl_iterate(ctx, f, u0, u_out, W: int, H: int, pitch: int, iterations: int,
                            ctypes.byref(st) if st is not None else None)
     _check(rc, ctx)
     return st
+
+
+def rl_iterate_tiles(ctx, jobs) -> None:
+    """Batched (request, tile) form: ``jobs`` is a sequence of
+    ``(f, u0, u_out, W, H, pitch, iterations)`` on the device, all under the
+    context's PSF (disc or box kernel)."""
+    arr = (rl_job * max(len(jobs), 1))()
+    for i, (f, u0, u_out, W, H, pitch, iterations) in enumerate(jobs):
+        arr[i] = rl_job(_addr(f), _addr(u0), _addr(u_out), None, None, W, H, pitch, iterations,
+                        rl_psf_desc(), None)
+    rc = load().rl_iterate_tiles(ctx, arr, len(jobs))
+    _check(rc, ctx)
 
 
 def rl_get_mask(ctx, dst, dst_pitch: int) -> None:
