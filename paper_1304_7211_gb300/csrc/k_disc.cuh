@@ -347,21 +347,26 @@ struct BoxOp {
 // Uniform rectangle of any size and anchor within the halo R (Sec. 3,
 // rectangular blur: separable sliding sums), given at run time as the tap
 // offsets [lox, hix] x [loy, hiy] about the anchor.  The prepass forms the
-// vertical sums V(r, c) of every staged column for the tile's rows, in a
-// separate plane; each block then slides the horizontal sums along V.  Both
-// passes cost O(1) per pixel whatever the rectangle's size.
+// vertical sums V(r, c) of every staged column for the tile's rows and
+// writes them over the staged tile (all reads finish, in registers, before
+// the first write); each block then slides the horizontal sums along V.
+// Both passes cost O(1) per pixel whatever the rectangle's size, and the
+// shared memory is the staged tile's alone.
 template <int R>
 struct RectOp {
     static constexpr int kR = R;
     static constexpr bool kUniform = true;
     static constexpr bool kPrepass = true;
+    static constexpr int kExtraFloats = 0;
     using G = Halo<R>;
     // V row pitch: a multiple of 8, room for the column skew (one float per
     // 32 columns) and the row skew (2 ((r >> 2) & 3)), which together keep the
     // 32 lanes of a warp -- 8 columns 8 apart x 4 rows 4 apart -- on distinct
     // banks
-    static constexpr int VP = (G::HP + G::HP / 32 + 7 + 7) / 8 * 8;
-    static constexpr int kExtraFloats = TY * VP;
+    static constexpr int VP = (G::HP + (G::HP - 1) / 32 + 6 + 7) / 8 * 8;
+    static_assert(TY * VP <= G::NR * G::HP, "V must fit over the staged tile");
+    static constexpr int NG = TY / 16;                      // 16-row groups per column
+    static constexpr int NI = (G::HP * NG + 127) / 128;     // (column, group) items per thread
     struct Params { int lox, hix, loy, hiy; };
     static __device__ __forceinline__ int vidx(int r, int c) { return r * VP + c + (c >> 5) + 2 * ((r >> 2) & 3); }
     // staged-tile index of logical column c of staged row m (16-byte units swizzled)
@@ -372,18 +377,32 @@ struct RectOp {
     // c(p) = sum_t q(p + t).  A column's sum slides down 16 rows, then
     // restarts (bounded FP32 drift).
     template <bool FWD>
-    static __device__ __forceinline__ void prepass(const float *tile, float *V, const Params &p) {
+    static __device__ __forceinline__ void prepass(float *tile, float *, const Params &p) {
         const int dlo = FWD ? -p.hiy : p.loy, dhi = FWD ? -p.loy : p.hiy;
-        constexpr int NG = TY / 16;
-        for (int it = threadIdx.x; it < G::HP * NG; it += 128) {
-            const int c = it % G::HP, r0 = it / G::HP * 16;
-            float s = 0.f;
-            for (int d = dlo; d <= dhi; ++d) s += tile[sidx(r0 + R + d, c)];
-            V[vidx(r0, c)] = s;
-#pragma unroll 5
-            for (int r = r0 + 1; r < r0 + 16; ++r) {
-                s += tile[sidx(r + R + dhi, c)] - tile[sidx(r - 1 + R + dlo, c)];
-                V[vidx(r, c)] = s;
+        float v[NI][16];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            const int it = threadIdx.x + 128 * k;
+            if (it < G::HP * NG) {
+                const int c = it % G::HP, r0 = it / G::HP * 16;
+                float s = 0.f;
+                for (int d = dlo; d <= dhi; ++d) s += tile[sidx(r0 + R + d, c)];
+                v[k][0] = s;
+#pragma unroll
+                for (int r = 1; r < 16; ++r) {
+                    s += tile[sidx(r0 + r + R + dhi, c)] - tile[sidx(r0 + r - 1 + R + dlo, c)];
+                    v[k][r] = s;
+                }
+            }
+        }
+        __syncthreads();  // every staged value read: V may overwrite the tile
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            const int it = threadIdx.x + 128 * k;
+            if (it < G::HP * NG) {
+                const int c = it % G::HP, r0 = it / G::HP * 16;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) tile[vidx(r0 + r, c)] = v[k][r];
             }
         }
     }
@@ -391,7 +410,7 @@ struct RectOp {
     template <bool FWD>
     static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
                                                  const Params &p) {
-        const float *V = tile + G::NR * G::HP;
+        const float *V = tile;  // the prepass wrote V over the staged tile
         const int elo = FWD ? -p.hix : p.lox, ehi = FWD ? -p.lox : p.hix;
         const int c0 = bx * SX + G::R4 + elo;  // V column of output 0's first term
 #pragma unroll
