@@ -75,7 +75,7 @@ typedef enum {
     RL_PATH_AUTO = 0,    /* motion -> RUNSUM, disc -> SPAN; dense -> STENCIL,
                             except -> SPAN: a uniform centred odd square up to
                             33 x 33 (box, Sec. 3 rectangular blur), another
-                            uniform rectangle reaching 4..16 pixels from the
+                            uniform rectangle reaching 3..16 pixels from the
                             anchor, and other uniform taps reaching more than
                             4 pixels                                            */
     RL_PATH_RUNSUM = 1,  /* sliding-window box filter along x or y (motion only)  */

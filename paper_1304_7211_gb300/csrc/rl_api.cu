@@ -505,10 +505,10 @@ int choose_path(const rl_ctx *ctx, int W) {
         else if (ctx->kind == RL_PSF_DISC) p = RL_PATH_SPAN;
         // a uniform centred square: the box kernel beats the stencil's taps
         // at every size; another uniform rectangle: the rectangle kernel,
-        // except within 3 pixels of the anchor, where the register stencil
-        // (K <= 7) is faster than its shared-memory passes
+        // except within 2 pixels of the anchor, where the register stencil
+        // (K <= 5) is as fast as its shared-memory passes
         else if (ctx->box_radius) p = RL_PATH_SPAN;
-        else if (ctx->rect && !(ctx->sq_k && ctx->sq_k <= 7)) p = RL_PATH_SPAN;
+        else if (ctx->rect && !(ctx->sq_k && ctx->sq_k <= 5)) p = RL_PATH_SPAN;
         // dense taps within 4 pixels of the anchor: the register-blocked
         // stencil beats span sums (every tap a register operand)
         else if (ctx->sq_k) p = RL_PATH_STENCIL;

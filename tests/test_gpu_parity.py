@@ -188,10 +188,10 @@ def test_uniform_box_and_rectangle_reduced_storage(storage, shape):
 
 def test_uniform_rectangle_from_dense_taps_auto_path():
     # uniform centred squares: the box kernel; other uniform rectangles
-    # within 3 pixels of the anchor: the register stencil; up to 16: the
+    # within 2 pixels of the anchor: the register stencil; up to 16: the
     # rectangle kernel; beyond: the span tiles
     for shape, path in (((3, 5), 3), ((3, 11), 2), ((13, 1), 2), ((5, 5), 2), ((35, 35), 2), ((3, 41), 2),
-                        ((9, 7), 2)):
+                        ((9, 7), 2), ((7, 3), 2)):
         spec = synth.dense(np.ones(shape))
         f32 = case(150, 90, spec)
         u, st = gpu_rl(spec, f32, 40)
