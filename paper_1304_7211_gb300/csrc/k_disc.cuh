@@ -1,7 +1,10 @@
 // k_disc.cuh -- the register-blocked two-half RL iteration (Eq. 3): the
-// generic box filter for the defocus disc (Sec. 3 "Defocus blur") and the
-// direct stencil for taps within 4 pixels of the anchor, one output tile per
-// CTA, a block operation policy for the convolution.
+// generic box filter for the defocus disc (Sec. 3 "Defocus blur"), separable
+// sliding sums for the square box and any uniform rectangle (Sec. 3
+// "Rectangular blur"), and the direct stencil for taps within 4 pixels of
+// the anchor; one output tile per CTA, a block operation policy for the
+// convolution (DiscOp, BoxOp, RectOp, StencilOp).  The tile body serves both
+// the single-image kernel and the batched (request, tile) kernel.
 //
 // Disc (DiscOp<R>): the disc of radius R (pixel-centre inclusion) is a stack
 // of horizontal runs; PSF row ty covers tx in [-s(ty), s(ty)],
