@@ -61,6 +61,7 @@ def test_null_arguments_return_status_without_gpu(lib):
     assert lib.rl_destroy(None) == rl.RL_OK
     assert lib.rl_iterate(None, None, None, None, 1, 1, 1, 1, None, None) == rl.RL_ERR_INVALID_ARG
     assert lib.rl_set_psf(None, None) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_iterate_tiles(None, None, 0) == rl.RL_ERR_INVALID_ARG
 
 
 def test_create_fails_loudly_without_gpu(lib):
