@@ -289,12 +289,12 @@ const char *rl_batch_last_error(const rl_batch *b);
  * run as one forward and one adjoint launch per iteration over the 64 x 64
  * tiles of every job still iterating, so many small images fill the GPU
  * that one image alone would leave mostly idle.  A job leaves the work list
- * when its own iteration count ends; each job's result is the image that
- * rl_iterate gives for it alone.
+ * when its own iteration count ends; each job's result is, bit for bit, the
+ * image that rl_iterate on ctx gives for it alone.
  *   ctx: its PSF must take the disc or box kernel (RL_PSF_DISC of radius
  *       1..16, or dense taps forming a uniform centred odd square up to
- *       33 x 33); FP32 storage; no exact-transpose band (clamp with
- *       RL_FLAG_ADJOINT_TRANSPOSE).
+ *       33 x 33); path AUTO or SPAN; FP32 storage; no exact-transpose band
+ *       (clamp with RL_FLAG_ADJOINT_TRANSPOSE).
  *   jobs[j]: f, u0 (NULL = f), u_out device pointers, caller-owned, valid
  *       until the work is done; u_out may alias u0 but not f; W, H, pitch
  *       (elements), iterations.  psf is ignored (ctx's PSF applies); thin,

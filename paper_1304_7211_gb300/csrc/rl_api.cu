@@ -1164,6 +1164,8 @@ extern "C" rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n) {
         return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate_tiles: FP32 storage only");
     if (needs_fold(ctx))
         return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate_tiles: no exact-transpose band in the batched form");
+    if (ctx->path_pref != RL_PATH_AUTO && ctx->path_pref != RL_PATH_SPAN)
+        return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate_tiles: runs the span path (AUTO or SPAN) only");
     int op = -1, R = 0;
     if (ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 && ctx->disc_radius <= rl::kDiscMaxRadius) {
         op = 0;
