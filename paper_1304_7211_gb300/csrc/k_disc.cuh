@@ -8,10 +8,12 @@
 //
 // Disc (DiscOp<R>): the disc of radius R (pixel-centre inclusion) is a stack
 // of horizontal runs; PSF row ty covers tx in [-s(ty), s(ty)],
-// s(ty) = floor(sqrt(R^2 - ty^2)).  Each thread owns a block of SY x SX
-// outputs.  For every input row the block touches, it loads the row segment
-// [x0 - R, x0 + SX + R) once from shared memory, forms its running (prefix)
-// sum in registers -- short, so FP32 stays accurate -- and adds to each
+// s(ty) = floor(sqrt(R^2 - ty^2)).  After staging, one pass turns every
+// staged row into its exclusive prefix sum in place (one thread per row; a
+// row of at most 64 + 2 * 16 values keeps FP32 prefix differences accurate
+// to a few ulps of the row sum).  Each thread owns a block of SY x SX
+// outputs: for every input row the block touches it loads the prefix entries
+// its runs end on -- a compile-time subset of its window -- and adds to each
 // output row that uses this input row the run sum P[j + R + 1 + s] -
 // P[j + R - s]: sliding the PSF only exchanges the run ends (Sec. 3), and
 // with a prefix a run of any length costs one difference.  R is a template
@@ -75,18 +77,35 @@ __device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_sr
 // 4-byte copies of the boundary-mapped pixels; the caller waits
 // (cp_async_wait_all) before the barrier.  16-bit storage goes through
 // registers, converted to FP32, several units in flight per thread.
-template <typename T, int nrows, int nu>
+template <typename T, int nrows, int nu, int pitch>
 __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, int y0, int xs, const T *src,
                                            long long sp, int tid) {
     constexpr int total = nrows * nu;
     if constexpr (sizeof(T) == 4) {
         const float *s = reinterpret_cast<const float *>(src);
+        // Interior tile with 16-byte aligned rows: warp w copies rows w, w + 4,
+        // ..., lane l unit l of each (nu <= 32), no boundary map.
+        if (nu <= 32 && y0 >= 0 && y0 + nrows <= H && xs >= 0 && xs + 4 * nu <= W &&
+            ((reinterpret_cast<uintptr_t>(s) | (uintptr_t)(sp * 4)) & 15) == 0) {
+            const int lane = tid & 31, w = tid >> 5;
+            if (lane < nu) {
+                const float *g = s + (long long)(y0 + w) * sp + xs + 4 * lane;
+                float *d = dst + w * pitch + (hunit(lane) << 2);
+#pragma unroll 4
+                for (int r = w; r < nrows; r += 4) {
+                    cp_async16(d, g);
+                    g += 4 * sp;
+                    d += 4 * pitch;
+                }
+            }
+            return;
+        }
         for (int e = tid; e < total; e += 128) {
             const int r = e / nu, u = e - r * nu;
             const int yy = bmap(y0 + r, H, clamp);
             const float *srow = s + (long long)yy * sp;
             const int x = xs + 4 * u;
-            float *d = dst + r * 4 * nu + (hunit(u) << 2);
+            float *d = dst + r * pitch + (hunit(u) << 2);
             if (x >= 0 && x + 4 <= W && (reinterpret_cast<uintptr_t>(srow) & 15) == 0) {
                 cp_async16(d, srow + x);
             } else {
@@ -132,19 +151,21 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
             const int e = e0 + 128 * b;
             if (e < total) {
                 const int r = e / nu, u = e - r * nu;
-                *reinterpret_cast<float4 *>(dst + r * 4 * nu + (hunit(u) << 2)) =
+                *reinterpret_cast<float4 *>(dst + r * pitch + (hunit(u) << 2)) =
                     make_float4(v[b][0], v[b][1], v[b][2], v[b][3]);
             }
         }
     }
 }
 
-// Geometry of the staged halo tile for a filter of radius R.
-template <int R>
+// Geometry of the staged halo tile for a filter of radius R; XU spare units
+// at the end of every row (the disc's row prefix has one more entry than
+// the row has columns).
+template <int R, int XU = 0>
 struct Halo {
     static constexpr int R4 = round4(R);           // halo rounded up to whole units
     static constexpr int NU = (TX + 2 * R4) / 4;   // units per row (even)
-    static constexpr int HP = 4 * NU;              // row pitch in floats
+    static constexpr int HP = 4 * (NU + XU);       // row pitch in floats
     static constexpr int NR = TY + 2 * R;          // staged rows
     static constexpr int NWU = (SX + 2 * R4) / 4;  // units in one block's window
     static constexpr int OFF = R4 - R;             // window column of offset -R
@@ -156,16 +177,16 @@ struct Halo {
 // 16-byte loads; the partial units at the two ends load only the columns in
 // use (8- or 4-byte loads: for a warp those take no more shared-memory
 // wavefronts than one 16-byte load, and they keep no dead registers).
-template <int R>
-__device__ __forceinline__ void load_window(const float *row, int bx, float (&w)[SX + 2 * R]) {
-    using G = Halo<R>;
-    constexpr int NW = SX + 2 * R;
+template <int R, int NW>
+__device__ __forceinline__ void load_window_n(const float *row, int bx, float (&w)[NW]) {
+    constexpr int OFF = round4(R) - R;      // window column of offset -R
+    constexpr int NWU = (OFF + NW + 3) / 4;  // units the window touches
 #pragma unroll
-    for (int t = 0; t < G::NWU; ++t) {
+    for (int t = 0; t < NWU; ++t) {
         const float *p = row + (hunit(2 * bx + t) << 2);
-        const int lo = G::OFF - 4 * t > 0 ? G::OFF - 4 * t : 0;
-        const int hi = G::OFF + NW - 4 * t < 4 ? G::OFF + NW - 4 * t : 4;
-        const int d = 4 * t - G::OFF;  // w index of unit column 0
+        const int lo = OFF - 4 * t > 0 ? OFF - 4 * t : 0;
+        const int hi = OFF + NW - 4 * t < 4 ? OFF + NW - 4 * t : 4;
+        const int d = 4 * t - OFF;  // w index of unit column 0
         if (lo == 0 && hi == 4) {
             const float4 v = *reinterpret_cast<const float4 *>(p);
             w[d] = v.x; w[d + 1] = v.y; w[d + 2] = v.z; w[d + 3] = v.w;
@@ -187,6 +208,11 @@ __device__ __forceinline__ void load_window(const float *row, int bx, float (&w)
     }
 }
 
+template <int R>
+__device__ __forceinline__ void load_window(const float *row, int bx, float (&w)[SX + 2 * R]) {
+    load_window_n<R, SX + 2 * R>(row, bx, w);
+}
+
 // Sum of the disc over the block's SY x SX outputs.  Input row m of the
 // block is array row row0 + m; output row i uses it with ty = i + R - m
 // (forward) -- the adjoint reads the mirrored offset, which has the same run.
@@ -205,30 +231,146 @@ __device__ __forceinline__ void f2add(unsigned long long &acc, unsigned long lon
     asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(d));
 }
 
+// Disc geometry: spare units at the end of every staged row hold the row
+// prefix's last entry (at unit hunit(NU), which is NU or NU + 1).  Three of
+// them make the row pitch an odd number of units, so the prefix pass (one
+// thread per row, all at the same unit) puts 8 consecutive rows on 8
+// distinct bank quads.
+template <int R>
+using DiscHalo = Halo<R, 3>;
+
+// Exclusive prefix of every staged row, in place: logical column k of a row
+// (0 <= k <= 4 NU, the last in the spare unit) becomes the sum of columns
+// [0, k).  One thread per row, a unit at a time.
+template <int R>
+__device__ __forceinline__ void row_prefix(float *tile) {
+    using G = DiscHalo<R>;
+    static_assert(G::NR <= 128, "one thread per staged row");
+    if (threadIdx.x < G::NR) {
+        float *row = tile + threadIdx.x * G::HP;
+        float acc = 0.f;
+#pragma unroll
+        for (int u = 0; u < G::NU; ++u) {
+            float4 *p = reinterpret_cast<float4 *>(row + (hunit(u) << 2));
+            const float4 v = *p;
+            float4 o;
+            o.x = acc;
+            o.y = o.x + v.x;
+            o.z = o.y + v.y;
+            o.w = o.z + v.z;
+            acc = o.w + v.w;
+            *p = o;
+        }
+        row[hunit(G::NU) << 2] = acc;
+    }
+}
+
+// Which prefix entries of its window a block reads in input row m: bit k of
+// mask[m] is set when some output row i < SY uses row m (PSF row ty = i + R -
+// m) and some output column j < SX has a run end at k, i.e. k = j + R - s or
+// k = j + R + 1 + s with s = s(ty).  Rows near the top and bottom of the disc
+// use short runs, so whole units of the window go unread there.
+template <int R>
+struct DiscNeed {
+    static constexpr int NP = SX + 2 * R + 1;
+    static constexpr int NR = SY + 2 * R;
+    struct Table { unsigned long long mask[NR]; };
+    static constexpr Table make() {
+        Table t{};
+        for (int m = 0; m < NR; ++m) {
+            unsigned long long b = 0;
+            for (int i = 0; i < SY; ++i) {
+                const int ty = i + R - m;
+                if (ty < -R || ty > R) continue;
+                const int s = run_half_width(R, ty);
+                for (int j = 0; j < SX; ++j) b |= (1ull << (j + R - s)) | (1ull << (j + R + 1 + s));
+            }
+            t.mask[m] = b;
+        }
+        return t;
+    }
+};
+
+// Load the prefix entries of input row m that the block reads (DiscNeed):
+// per 16-byte unit of the window, the needed span only -- one 16-byte load
+// when it is the whole unit, else 8- and 4-byte loads.  Entries left out are
+// never read.
+template <int R, int NW>
+struct WinUnits {
+    static constexpr int OFF = round4(R) - R;
+    static constexpr int N = (OFF + NW + 3) / 4;  // units a window touches
+};
+
+// up[t] points at unit t of the block's window in its first input row; row m
+// adds m * HP, a compile-time offset.
+template <int R, int NW>
+__device__ __forceinline__ void load_needed(const float *const (&up)[WinUnits<R, NW>::N], int roff,
+                                            unsigned long long need, float (&w)[NW]) {
+    constexpr int OFF = WinUnits<R, NW>::OFF;
+    constexpr int NWU = WinUnits<R, NW>::N;
+#pragma unroll
+    for (int t = 0; t < NWU; ++t) {
+        const float *p = up[t] + roff;
+        const int d = 4 * t - OFF;  // w index of unit column 0
+        int lo = 4, hi = 0;         // needed columns [lo, hi) of this unit
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = d + k;
+            if (i >= 0 && i < NW && ((need >> i) & 1ull)) {
+                lo = lo < k ? lo : k;
+                hi = hi > k + 1 ? hi : k + 1;
+            }
+        }
+        if (lo >= hi) continue;
+        if (lo == 0 && hi == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p);
+            w[d] = v.x; w[d + 1] = v.y; w[d + 2] = v.z; w[d + 3] = v.w;
+            continue;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < lo || k >= hi) continue;
+            const bool pair_head = (k & 1) == 0 && k + 1 < hi;
+            const bool pair_tail = (k & 1) == 1 && k - 1 >= lo;
+            if (pair_head) {
+                const float2 v = *reinterpret_cast<const float2 *>(p + k);
+                w[d + k] = v.x;
+                w[d + k + 1] = v.y;
+            } else if (!pair_tail) {
+                w[d + k] = p[k];
+            }
+        }
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&out)[SY][SX]) {
-    using G = Halo<R>;
-    constexpr int NW = SX + 2 * R;
-    constexpr int NR = SY + 2 * R;
+    using G = DiscHalo<R>;
+    using N = DiscNeed<R>;
+    constexpr int NP = N::NP;  // prefix entries in a block's window
+    constexpr int NR = N::NR;
+    constexpr typename N::Table need = N::make();  // folded: m is unrolled
     // accumulators of output columns (2h, 2h + 1) as packed pairs
     unsigned long long acc[SY][SX / 2];
 #pragma unroll
     for (int i = 0; i < SY; ++i)
 #pragma unroll
         for (int h = 0; h < SX / 2; ++h) acc[i][h] = 0ull;
-    const float *base = tile + row0 * G::HP;
-    // The window of the next input row is loaded while the current one is
-    // summed, so shared-memory latency overlaps the additions.
-    float w[NW];
-    load_window<R>(base, bx, w);
+    // unit pointers of the window in the first input row, computed once
+    constexpr int NWU = WinUnits<R, NP>::N;
+    const float *up[NWU];
+#pragma unroll
+    for (int t = 0; t < NWU; ++t) up[t] = tile + row0 * G::HP + (hunit(2 * bx + t) << 2);
+    // P[k] is the row prefix at the block's window column k (column offset
+    // k - R from its first output): the run [j - s, j + s] of output j sums
+    // to P[j + R + 1 + s] - P[j + R - s].  The next input row's entries are
+    // loaded while the current ones are used.
+    float P[NP];
+    load_needed<R, NP>(up, 0, need.mask[0], P);
 #pragma unroll
     for (int m = 0; m < NR; ++m) {
-        float wn[NW];
-        if (m + 1 < NR) load_window<R>(base + (m + 1) * G::HP, bx, wn);
-        float P[NW + 1];
-        P[0] = 0.f;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) P[k + 1] = P[k] + w[k];
+        float Pn[NP];
+        if (m + 1 < NR) load_needed<R, NP>(up, (m + 1) * G::HP, need.mask[m + 1], Pn);
 #pragma unroll
         for (int i = 0; i < SY; ++i) {
             const int ty = i + R - m;
@@ -242,7 +384,8 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
         }
         if (m + 1 < NR) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) w[k] = wn[k];
+            for (int k = 0; k < NP; ++k)
+                if ((need.mask[m + 1] >> k) & 1ull) P[k] = Pn[k];
         }
     }
 #pragma unroll
@@ -252,17 +395,23 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
 }
 
 // Block operations of the generic half-iteration kernel.  kR is the halo
-// radius, kUniform says whether the result still has to be scaled by the
-// uniform tap weight, Params travels in the kernel's parameter block.  An op
-// with kPrepass runs prepass() over the staged tile (all threads, then a
-// barrier) before the blocks, into kExtraFloats of shared memory after it.
+// radius, Geom the staged tile's geometry, kUniform says whether the result
+// still has to be scaled by the uniform tap weight, Params travels in the
+// kernel's parameter block.  An op with kPrepass runs prepass() over the
+// staged tile (all threads, then a barrier) before the blocks, into
+// kExtraFloats of shared memory after it.
 template <int R>
 struct DiscOp {
     static constexpr int kR = R;
+    using Geom = DiscHalo<R>;
     static constexpr bool kUniform = true;
-    static constexpr bool kPrepass = false;
+    static constexpr bool kPrepass = true;
     static constexpr int kExtraFloats = 0;
     struct Params {};
+    template <bool FWD>
+    static __device__ __forceinline__ void prepass(float *tile, float *, const Params &) {
+        row_prefix<R>(tile);
+    }
     template <bool FWD>
     static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
                                                  const Params &) {
@@ -336,6 +485,7 @@ __device__ __forceinline__ void box_block(const float *tile, int row0, int bx, f
 template <int R>
 struct BoxOp {
     static constexpr int kR = R;
+    using Geom = Halo<R>;
     static constexpr bool kUniform = true;
     static constexpr bool kPrepass = false;
     static constexpr int kExtraFloats = 0;
@@ -358,6 +508,7 @@ struct BoxOp {
 template <int R>
 struct RectOp {
     static constexpr int kR = R;
+    using Geom = Halo<R>;
     static constexpr bool kUniform = true;
     static constexpr bool kPrepass = true;
     static constexpr int kExtraFloats = 0;
@@ -437,6 +588,7 @@ struct RectOp {
 template <int K>
 struct StencilOp {
     static constexpr int kR = K / 2;
+    using Geom = Halo<K / 2>;
     static constexpr bool kUniform = false;
     static constexpr bool kPrepass = false;
     static constexpr int kExtraFloats = 0;
@@ -573,7 +725,7 @@ __device__ __forceinline__ void st_mask8(uint8_t *p, int n, unsigned long long v
 // Seven resident CTAs per SM (<= 72 registers) while the staged halo allows
 // it; the selective-convolution variant needs more registers.
 template <int R, bool THIN>
-constexpr int min_blocks() { return R > 8 ? 4 : THIN || R == 1 ? 5 : 7; }
+constexpr int min_blocks() { return R > 12 ? 5 : R > 8 ? 6 : THIN || R == 1 ? 5 : 7; }
 
 // One 64 x 64 output tile (tbx, tby) of a half-iteration, run by the whole
 // CTA; the kernels below call it once per CTA.
@@ -581,7 +733,7 @@ template <typename T, bool THIN, typename Op, bool FWD>
 __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                                           long long q_pitch, int tbx, int tby) {
     constexpr int R = Op::kR;
-    using G = Halo<R>;
+    using G = typename Op::Geom;
     extern __shared__ float sm[];
     const int x0 = tbx * TX, y0 = tby * TY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -592,11 +744,23 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + tby * a.tiles_x + tbx : nullptr;
     if (tflag && !a.full && *tflag == 0) return;
     if (FWD)
-        stage_halo<T, G::NR, G::NU>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
+        stage_halo<T, G::NR, G::NU, G::HP>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
                                     threadIdx.x);
     else
-        stage_halo<float, G::NR, G::NU>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
+        stage_halo<float, G::NR, G::NU, G::HP>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
                                         threadIdx.x);
+    {
+        // The epilogue reads f (forward) or u (adjoint) at the tile's pixels:
+        // start moving those rows into L2 now, while the halo lands and the
+        // blocks are summed.  Thread t covers 128 bytes of row t / L.
+        constexpr int L = (TX * (int)sizeof(T) + 127) / 128;  // 128-byte lines per tile row
+        const int y = y0 + threadIdx.x / L, x = x0 + (threadIdx.x % L) * (128 / (int)sizeof(T));
+        if (threadIdx.x < TY * L && y < a.H && x < a.W) {
+            const T *p = FWD ? (const T *)a.f + (long long)y * a.f_pitch + x
+                             : (const T *)a.u_in + (long long)y * a.in_pitch + x;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
     if constexpr (Op::kPrepass) {
@@ -781,7 +945,7 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, false>())
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                        long long q_pitch, cudaStream_t s) {
-    constexpr size_t smem = Halo<Op::kR>::bytes + Op::kExtraFloats * sizeof(float);
+    constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
     cudaError_t e = ensure_smem<k_disc_half<T, THIN, Op, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
@@ -806,7 +970,7 @@ template <typename Op>
 cudaError_t launch_op_tiles(const TileJob *jobs, const int2 *items, int n_items, int phase,
                             const typename Op::Params &prm, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
-    constexpr size_t smem = Halo<Op::kR>::bytes + Op::kExtraFloats * sizeof(float);
+    constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
     cudaError_t e = ensure_smem<k_disc_half_tiles<Op, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half_tiles<Op, false>>(smem);
     if (e != cudaSuccess) return e;
