@@ -316,11 +316,15 @@ const char *rl_version(void);
  * where an allocation may block on the device, processes whose device memory
  * is partitioned in advance.
  *
- * Runs `iterations` RL iterations (Eq. 3) for horizontal linear motion blur
- * of `length` pixels (RL_PSF_MOTION, axis 0), FP32, `boundary` as in
+ * Runs `iterations` RL iterations of the running-sum path for horizontal
+ * linear motion blur of `length` pixels (RL_PSF_MOTION, axis 0), FP32,
+ * `boundary` as in
  * rl_boundary, on `stream` (cudaStream_t; NULL = default stream) of the
  * CURRENT device.  f, u0 (NULL = f) and u_out are caller-owned device
- * pointers with row pitch `pitch` elements; u_out must alias neither f nor u0.
+ * pointers of the current device (or managed memory) with row pitch `pitch`
+ * elements; anything else -- a host buffer, another device's memory -- is
+ * rejected with RL_ERR_INVALID_ARG before any launch, since staging it would
+ * allocate.  u_out must alias neither f nor u0.
  * No context is needed and the call allocates nothing: its only scratch (the
  * second buffer of the iteration ping-pong) is a fixed array of
  * RL_NOALLOC_MAX_PIXELS floats (16 MiB) in the library image, which every GPU
@@ -329,6 +333,7 @@ const char *rl_version(void);
  *
  * The first call on each device looks up the array's device address (once,
  * with that device current); make that first call before any stream capture.
+ * The cached address does not survive a cudaDeviceReset of that device.
  * All calls on a device share the array and it keeps the last call's
  * contents; nothing in it needs clearing (every pixel is written before it is
  * read), but calls whose work overlaps on the GPU race on it.  Returns when

@@ -35,6 +35,19 @@ void set_err(char *err, int err_len, const char *msg) {
     if (err && err_len > 0) snprintf(err, (size_t)err_len, "%s", msg);
 }
 
+// Device (or managed) memory of device `dev`.  The entry point cannot stage a
+// host buffer the way rl_iterate does (that would allocate), so anything else
+// is rejected before a kernel could dereference it.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 }  // namespace
 
 extern "C" rl_status rl_motion_x_noalloc(const float *f, const float *u0, float *u_out, int W,
@@ -73,10 +86,17 @@ extern "C" rl_status rl_motion_x_noalloc(const float *f, const float *u0, float 
         set_err(err, err_len, "rl_motion_x_noalloc: no current CUDA device");
         return RL_ERR_CUDA;
     }
+    if (!on_device(f, dev) || !on_device(u_out, dev) || (u0 && !on_device(u0, dev))) {
+        set_err(err, err_len, "rl_motion_x_noalloc: f, u0 and u_out must be device memory of the "
+                              "current device (host buffers cannot be staged without allocating)");
+        return RL_ERR_INVALID_ARG;
+    }
     float *scratch = nullptr;
     {
         // One-time set-up per device, with that device current: the host-side
-        // name of the array is not a device address, so ask the runtime.
+        // name of the array is not a device address, so ask the runtime.  The
+        // cached address belongs to the device's primary context and does not
+        // survive a cudaDeviceReset.
         std::lock_guard<std::mutex> lock(g_setup_mu);
         if (!g_scratch_addr[dev]) {
             void *p = nullptr;

@@ -233,7 +233,18 @@ def rl_get_mask(ctx, dst, dst_pitch: int) -> None:
 def rl_motion_x_noalloc(f, u0, u_out, W: int, H: int, pitch: int, length: int,
                         boundary="mirror", iterations: int = 1, stream=None) -> None:
     """Allocation-free running-sum RL for horizontal motion blur (FP32, device
-    pointers, current device); see include/rl.h.  Raises RLError on failure."""
+    pointers, current device); see include/rl.h.  Raises RLError on failure.
+
+    f, u0 (or None) and u_out are FP32 CUDA tensors (or raw device addresses
+    as int): this entry point cannot stage host memory, so numpy arrays, CPU
+    tensors and other dtypes are refused here, before the library is called."""
+    for name, t in (("f", f), ("u0", u0), ("u_out", u_out)):
+        if t is None and name == "u0":
+            continue
+        if isinstance(t, int):
+            continue
+        if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.float32":
+            raise TypeError(f"rl_motion_x_noalloc: {name} must be a float32 CUDA tensor or a device address")
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     buf = ctypes.create_string_buffer(256)

@@ -66,3 +66,54 @@ def test_noalloc_rejects_images_beyond_the_fixed_scratch():
         rl.rl_motion_x_noalloc(f, None, f.clone(), W, H, W, 5, "mirror", 3)
     assert e.value.status == rl.RL_ERR_INVALID_ARG
     assert "exceeds the fixed scratch" in e.value.message
+
+
+@pytest.mark.parametrize("iters", [7, 8])
+def test_noalloc_padded_pitch_and_start_image(iters):
+    """Padded rows (pitch W + 37) and an explicit start image: the ping-pong
+    then alternates between the fixed array (pitch W) and u_out (the caller's
+    pitch), and the last iteration must land in u_out whether the count is
+    odd or even.  Compared with rl_iterate on the same padded buffers."""
+    from paper_1304_7211_gb300 import rl
+    torch.cuda.set_device(0)
+    spec = synth.motion(13, 0)
+    W, H, pad = 251, 173, 37
+    c = synth.make_case(W, H, spec, 0, "poisson", synth.SEED_BASE + 64)
+    fb = torch.zeros((H, W + pad), device="cuda")
+    fb[:, :W] = torch.from_numpy(c.f.astype(np.float32)).cuda()
+    u0b = torch.zeros_like(fb)
+    u0b[:, :W] = fb[:, :W] * 0.9 + 1.0
+    out = torch.full_like(fb, -1.0)
+    rl.rl_motion_x_noalloc(fb, u0b, out, W, H, W + pad, spec.length, "mirror", iters,
+                           torch.cuda.current_stream())
+    ref = torch.full_like(fb, -1.0)
+    with rl.Deconvolver(spec, path="runsum") as d:
+        rl.rl_iterate(d.ctx, fb, u0b, ref, W, H, W + pad, iters)
+    torch.cuda.synchronize()
+    err = oracle.rel_linf(out[:, :W].cpu().numpy(), ref[:, :W].cpu().numpy().astype(np.float64))
+    assert err <= TOL, err
+    # the padding columns of u_out are not touched
+    assert bool((out[:, W:] == -1.0).all())
+
+
+def test_noalloc_refuses_host_memory_before_any_launch():
+    """The entry point cannot stage host buffers (that would allocate), so a
+    numpy array or CPU tensor is refused by the binding, and a raw host
+    address by the library itself, before any kernel is launched."""
+    from paper_1304_7211_gb300 import rl
+    torch.cuda.set_device(0)
+    W, H = 64, 32
+    f_host = np.ones((H, W), np.float32)
+    out = torch.empty((H, W), device="cuda")
+    with pytest.raises(TypeError):
+        rl.rl_motion_x_noalloc(f_host, None, out, W, H, W, 5, "mirror", 2)
+    with pytest.raises(TypeError):
+        rl.rl_motion_x_noalloc(torch.ones((H, W)), None, out, W, H, W, 5, "mirror", 2)
+    with pytest.raises(TypeError):
+        rl.rl_motion_x_noalloc(torch.ones((H, W), device="cuda", dtype=torch.float16), None, out,
+                               W, H, W, 5, "mirror", 2)
+    with pytest.raises(rl.RLError) as e:
+        rl.rl_motion_x_noalloc(f_host.ctypes.data, None, out, W, H, W, 5, "mirror", 2)
+    assert e.value.status == rl.RL_ERR_INVALID_ARG
+    assert "device memory" in e.value.message
+    torch.cuda.synchronize()  # the context is still healthy
