@@ -135,9 +135,15 @@ typedef struct {
 } rl_thinning;
 
 /* rl_config.flags */
-#define RL_FLAG_PER_ITERATION 1 /* one launch per iteration even where the
-                                   running-sum path could keep whole rows
-                                   resident for all iterations            */
+#define RL_FLAG_PER_ITERATION 1 /* one launch per iteration (per half on
+                                   the disc path) even where the running-
+                                   sum path could keep whole rows resident
+                                   for all iterations, or the disc path run
+                                   them all in one persistent launch      */
+#define RL_FLAG_PERSISTENT 4    /* disc path: one persistent launch for all
+                                   iterations even where the image has too
+                                   few tiles for it to pay (about one tile
+                                   per resident CTA); tests and tuning    */
 /* The adjoint convolution of Eq. 3.  Default: h* (x) q with the same
  * boundary continuation as the forward one -- h reflected about the origin
  * (Sec. 2), the "pad-flip" operator B.  With this flag: the exact matrix
@@ -308,6 +314,20 @@ rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n);
 
 /* Library version string, e.g. "rl-gb300 0.1 sm_103a". */
 const char *rl_version(void);
+
+/*
+ * Self-test of failure detection in the persistent disc kernel (the one
+ * launch that runs every iteration of a plain disc solve; its work items wait
+ * for neighbouring tiles with bounded waits).  Runs a 128 x 128 launch on
+ * `device` whose first half is never handed out, so every later item waits
+ * for tiles that never finish; each wait gives up after wait_ms (1..10000)
+ * and the kernel records it and returns without faulting.  Returns
+ * RL_ERR_TIMEOUT when the give-up was detected and reported (the expected
+ * outcome), RL_ERR_STATE if the kernel finished without reporting it,
+ * RL_ERR_CUDA or RL_ERR_INVALID_ARG otherwise.  Allocates and frees its own
+ * small buffers; no context is needed.  No counterpart in the paper.
+ */
+rl_status rl_selftest_wait_timeout(int device, int wait_ms);
 
 /*
  * Allocation-free variant of the running-sum path.  The paper has no

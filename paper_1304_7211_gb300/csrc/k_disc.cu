@@ -47,6 +47,19 @@ cudaError_t launch_tiles(int op, int radius, const TileJob *jobs, const int2 *it
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_disc_persist(const PersistArgs &p, int storage, int radius, cudaStream_t s) {
+    switch (radius) {
+#define RL_PERSIST_CASE(R) \
+    case R: return launch_disc_persist_r##R(p, storage, s);
+    RL_PERSIST_CASE(1) RL_PERSIST_CASE(2) RL_PERSIST_CASE(3) RL_PERSIST_CASE(4) RL_PERSIST_CASE(5)
+    RL_PERSIST_CASE(6) RL_PERSIST_CASE(7) RL_PERSIST_CASE(8) RL_PERSIST_CASE(9) RL_PERSIST_CASE(10)
+    RL_PERSIST_CASE(11) RL_PERSIST_CASE(12) RL_PERSIST_CASE(13) RL_PERSIST_CASE(14) RL_PERSIST_CASE(15)
+    RL_PERSIST_CASE(16)
+#undef RL_PERSIST_CASE
+    }
+    return cudaErrorNotSupported;
+}
+
 cudaError_t launch_stencil(const IterArgs &a, const float *taps, int K, int storage, bool thin,
                            float *qplane, long long q_pitch, cudaStream_t s) {
     switch (K) {

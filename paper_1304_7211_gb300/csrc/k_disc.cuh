@@ -32,6 +32,7 @@
 // supplies A^T q on the border band.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "rl_launch.h"
@@ -42,6 +43,7 @@ namespace disc {
 constexpr int SX = 8;  // outputs per thread along x
 constexpr int SY = 4;  // outputs per thread along y
 constexpr int TX = 64, TY = 64;  // output tile of one CTA (128 threads)
+static_assert(TX == disc_tile() && TY == disc_tile(), "the host sizes tile arrays by disc_tile()");
 
 // Shared-memory layout of a staged halo tile: rows of 4-float units, the
 // halo rounded up to R4 = 4 ceil(R / 4) columns on each side so that every
@@ -70,6 +72,28 @@ __device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_sr
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 
+// Loads of data that other CTAs of the same grid write while it runs (the
+// persistent kernel's u and q planes) must come from L2, the point of
+// coherence: COH selects ld.global.cg for them.  Read-only data (f) and the
+// two-launch kernels keep the cached / non-coherent loads.
+template <bool COH, typename V>
+__device__ __forceinline__ V gld(const V *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return *p;
+}
+template <bool COH, typename T>
+__device__ __forceinline__ float gld_elem(const T *p, long long i) {
+    if constexpr (!COH) {
+        return Stor<T>::ld(p, i);
+    } else if constexpr (sizeof(T) == 4) {
+        return __ldcg(reinterpret_cast<const float *>(p) + i);
+    } else {
+        const unsigned short b = __ldcg(reinterpret_cast<const unsigned short *>(p) + i);
+        if constexpr (std::is_same<T, __half>::value) return __half2float(__ushort_as_half(b));
+        else return __bfloat162float(__ushort_as_bfloat16(b));
+    }
+}
+
 // Stage the halo tile: array row r, column c (r < nrows, c < 4 nu) is image
 // pixel (y0 + r, xs + c), continued across the border (clamp or mirror).
 // xs is a multiple of 4.  FP32 goes by asynchronous copies -- 16 bytes where
@@ -77,25 +101,30 @@ __device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_sr
 // 4-byte copies of the boundary-mapped pixels; the caller waits
 // (cp_async_wait_all) before the barrier.  16-bit storage goes through
 // registers, converted to FP32, several units in flight per thread.
-template <typename T, int nrows, int nu, int pitch>
+template <typename T, int nrows, int nu, int pitch, bool COH = false>
 __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, int y0, int xs, const T *src,
                                            long long sp, int tid) {
     constexpr int total = nrows * nu;
     if constexpr (sizeof(T) == 4) {
         const float *s = reinterpret_cast<const float *>(src);
         // Interior tile with 16-byte aligned rows: warp w copies rows w, w + 4,
-        // ..., lane l unit l of each (nu <= 32), no boundary map.
-        if (nu <= 32 && y0 >= 0 && y0 + nrows <= H && xs >= 0 && xs + 4 * nu <= W &&
+        // ..., lane l units l and l + 32 of each (nu <= 64), no boundary map.
+        static_assert(nu <= 64, "two units per lane");
+        if (y0 >= 0 && y0 + nrows <= H && xs >= 0 && xs + 4 * nu <= W &&
             ((reinterpret_cast<uintptr_t>(s) | (uintptr_t)(sp * 4)) & 15) == 0) {
             const int lane = tid & 31, w = tid >> 5;
-            if (lane < nu) {
-                const float *g = s + (long long)(y0 + w) * sp + xs + 4 * lane;
-                float *d = dst + w * pitch + (hunit(lane) << 2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int u = lane + 32 * h;
+                if (u < nu) {
+                    const float *g = s + (long long)(y0 + w) * sp + xs + 4 * u;
+                    float *d = dst + w * pitch + (hunit(u) << 2);
 #pragma unroll 4
-                for (int r = w; r < nrows; r += 4) {
-                    cp_async16(d, g);
-                    g += 4 * sp;
-                    d += 4 * pitch;
+                    for (int r = w; r < nrows; r += 4) {
+                        cp_async16(d, g);
+                        g += 4 * sp;
+                        d += 4 * pitch;
+                    }
                 }
             }
             return;
@@ -108,6 +137,9 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
             float *d = dst + r * pitch + (hunit(u) << 2);
             if (x >= 0 && x + 4 <= W && (reinterpret_cast<uintptr_t>(srow) & 15) == 0) {
                 cp_async16(d, srow + x);
+            } else if constexpr (COH) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[k] = __ldcg(srow + bmap(x + k, W, clamp));
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) cp_async4(d + k, srow + bmap(x + k, W, clamp));
@@ -127,7 +159,8 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
                 const int x = xs + 4 * u;
                 if (x >= 0 && x + 4 <= W && (reinterpret_cast<uintptr_t>(srow + x) & 7) == 0) {
                     // a whole unit inside the image: one 8-byte load of 4 values
-                    const uint2 w2 = __ldg(reinterpret_cast<const uint2 *>(srow + x));
+                    const uint2 w2 = COH ? __ldcg(reinterpret_cast<const uint2 *>(srow + x))
+                                         : __ldg(reinterpret_cast<const uint2 *>(srow + x));
                     const unsigned wv[2] = {w2.x, w2.y};
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
@@ -142,7 +175,7 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
                     }
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) v[b][k] = Stor<T>::ld(srow, bmap(x + k, W, clamp));
+                    for (int k = 0; k < 4; ++k) v[b][k] = gld_elem<COH>(srow, bmap(x + k, W, clamp));
                 }
             }
         }
@@ -161,12 +194,12 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
 // Geometry of the staged halo tile for a filter of radius R; XU spare units
 // at the end of every row (the disc's row prefix has one more entry than
 // the row has columns).
-template <int R, int XU = 0>
+template <int R, int XU = 0, int TXg = TX, int TYg = TY>
 struct Halo {
     static constexpr int R4 = round4(R);           // halo rounded up to whole units
-    static constexpr int NU = (TX + 2 * R4) / 4;   // units per row (even)
+    static constexpr int NU = (TXg + 2 * R4) / 4;  // units per row (even)
     static constexpr int HP = 4 * (NU + XU);       // row pitch in floats
-    static constexpr int NR = TY + 2 * R;          // staged rows
+    static constexpr int NR = TYg + 2 * R;         // staged rows
     static constexpr int NWU = (SX + 2 * R4) / 4;  // units in one block's window
     static constexpr int OFF = R4 - R;             // window column of offset -R
     static constexpr size_t bytes = (size_t)NR * HP * sizeof(float);
@@ -236,15 +269,15 @@ __device__ __forceinline__ void f2add(unsigned long long &acc, unsigned long lon
 // them make the row pitch an odd number of units, so the prefix pass (one
 // thread per row, all at the same unit) puts 8 consecutive rows on 8
 // distinct bank quads.
-template <int R>
-using DiscHalo = Halo<R, 3>;
+template <int R, int TXg = TX>
+using DiscHalo = Halo<R, 3, TXg>;
 
 // Exclusive prefix of every staged row, in place: logical column k of a row
 // (0 <= k <= 4 NU, the last in the spare unit) becomes the sum of columns
 // [0, k).  One thread per row, a unit at a time.
-template <int R>
+template <int R, int TXg>
 __device__ __forceinline__ void row_prefix(float *tile) {
-    using G = DiscHalo<R>;
+    using G = DiscHalo<R, TXg>;
     static_assert(G::NR <= 128, "one thread per staged row");
     if (threadIdx.x < G::NR) {
         float *row = tile + threadIdx.x * G::HP;
@@ -270,16 +303,16 @@ __device__ __forceinline__ void row_prefix(float *tile) {
 // m) and some output column j < SX has a run end at k, i.e. k = j + R - s or
 // k = j + R + 1 + s with s = s(ty).  Rows near the top and bottom of the disc
 // use short runs, so whole units of the window go unread there.
-template <int R>
+template <int R, int SYb>
 struct DiscNeed {
     static constexpr int NP = SX + 2 * R + 1;
-    static constexpr int NR = SY + 2 * R;
+    static constexpr int NR = SYb + 2 * R;
     struct Table { unsigned long long mask[NR]; };
     static constexpr Table make() {
         Table t{};
         for (int m = 0; m < NR; ++m) {
             unsigned long long b = 0;
-            for (int i = 0; i < SY; ++i) {
+            for (int i = 0; i < SYb; ++i) {
                 const int ty = i + R - m;
                 if (ty < -R || ty > R) continue;
                 const int s = run_half_width(R, ty);
@@ -343,17 +376,17 @@ __device__ __forceinline__ void load_needed(const float *const (&up)[WinUnits<R,
     }
 }
 
-template <int R>
-__device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&out)[SY][SX]) {
-    using G = DiscHalo<R>;
-    using N = DiscNeed<R>;
+template <int R, int TXg, int SYb>
+__device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&out)[SYb][SX]) {
+    using G = DiscHalo<R, TXg>;
+    using N = DiscNeed<R, SYb>;
     constexpr int NP = N::NP;  // prefix entries in a block's window
     constexpr int NR = N::NR;
     constexpr typename N::Table need = N::make();  // folded: m is unrolled
     // accumulators of output columns (2h, 2h + 1) as packed pairs
-    unsigned long long acc[SY][SX / 2];
+    unsigned long long acc[SYb][SX / 2];
 #pragma unroll
-    for (int i = 0; i < SY; ++i)
+    for (int i = 0; i < SYb; ++i)
 #pragma unroll
         for (int h = 0; h < SX / 2; ++h) acc[i][h] = 0ull;
     // unit pointers of the window in the first input row, computed once
@@ -372,7 +405,7 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
         float Pn[NP];
         if (m + 1 < NR) load_needed<R, NP>(up, (m + 1) * G::HP, need.mask[m + 1], Pn);
 #pragma unroll
-        for (int i = 0; i < SY; ++i) {
+        for (int i = 0; i < SYb; ++i) {
             const int ty = i + R - m;
             if (ty < -R || ty > R) continue;
             const int s = run_half_width(R, ty);
@@ -389,7 +422,7 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
         }
     }
 #pragma unroll
-    for (int i = 0; i < SY; ++i)
+    for (int i = 0; i < SYb; ++i)
 #pragma unroll
         for (int h = 0; h < SX / 2; ++h) f2unpack(acc[i][h], out[i][2 * h], out[i][2 * h + 1]);
 }
@@ -399,23 +432,37 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
 // still has to be scaled by the uniform tap weight, Params travels in the
 // kernel's parameter block.  An op with kPrepass runs prepass() over the
 // staged tile (all threads, then a barrier) before the blocks, into
-// kExtraFloats of shared memory after it.
-template <int R>
+// kExtraFloats of shared memory after it.  kTX x kTY is the output tile of
+// one CTA and kSY the rows of a thread's block (kSY x SX outputs); the ops
+// without these members use the default 64 x 64 tile and 4-row blocks.
+struct DefaultGeo {
+    static constexpr int kTX = TX, kTY = TY, kSY = SY;
+    static constexpr bool kWide = false;
+};
+
+// The disc on a TXg x 64 tile with SYb-row blocks.  Every form of the path
+// uses the default (64, 4).  A (128, 8) form reads each staged row's prefix
+// entries once for 8 output rows instead of 4 -- a third fewer shared-memory
+// wavefronts per output -- but needs 126-166 registers, leaves 12-16 warps
+// per SM and measured slower at every size and radius tried.
+template <int R, int TXg = TX, int SYb = SY>
 struct DiscOp {
     static constexpr int kR = R;
-    using Geom = DiscHalo<R>;
+    static constexpr int kTX = TXg, kTY = TY, kSY = SYb;
+    static constexpr bool kWide = TXg != TX;
+    using Geom = DiscHalo<R, TXg>;
     static constexpr bool kUniform = true;
     static constexpr bool kPrepass = true;
     static constexpr int kExtraFloats = 0;
     struct Params {};
     template <bool FWD>
     static __device__ __forceinline__ void prepass(float *tile, float *, const Params &) {
-        row_prefix<R>(tile);
+        row_prefix<R, TXg>(tile);
     }
     template <bool FWD>
-    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
+    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SYb][SX],
                                                  const Params &) {
-        disc_block<R>(tile, row0, bx, acc);  // symmetric: forward = adjoint
+        disc_block<R, TXg, SYb>(tile, row0, bx, acc);  // symmetric: forward = adjoint
     }
 };
 
@@ -483,7 +530,7 @@ __device__ __forceinline__ void box_block(const float *tile, int row0, int bx, f
 
 // Uniform (2R + 1)^2 box (Sec. 3, rectangular blur).
 template <int R>
-struct BoxOp {
+struct BoxOp : DefaultGeo {
     static constexpr int kR = R;
     using Geom = Halo<R>;
     static constexpr bool kUniform = true;
@@ -506,7 +553,7 @@ struct BoxOp {
 // Both passes cost O(1) per pixel whatever the rectangle's size, and the
 // shared memory is the staged tile's alone.
 template <int R>
-struct RectOp {
+struct RectOp : DefaultGeo {
     static constexpr int kR = R;
     using Geom = Halo<R>;
     static constexpr bool kUniform = true;
@@ -586,7 +633,7 @@ struct RectOp {
 // filter of Sec. 3 and 5): every tap is a compile-time offset into the
 // register window and a constant-bank operand of its FMA.
 template <int K>
-struct StencilOp {
+struct StencilOp : DefaultGeo {
     static constexpr int kR = K / 2;
     using Geom = Halo<K / 2>;
     static constexpr bool kUniform = false;
@@ -636,16 +683,16 @@ struct StencilOp {
 // the segment are issued before any is used (one memory round trip per row,
 // not per pixel) and go out as 16-byte accesses when the segment is whole
 // and aligned, else as n scalars.
-template <typename T>
+template <typename T, bool COH = false>
 __device__ __forceinline__ void ld_seg(const T *p, int n, float (&v)[SX]) {
     if (n == SX && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
         if constexpr (sizeof(T) == 4) {
-            const float4 a = reinterpret_cast<const float4 *>(p)[0];
-            const float4 b = reinterpret_cast<const float4 *>(p)[1];
+            const float4 a = gld<COH>(reinterpret_cast<const float4 *>(p));
+            const float4 b = gld<COH>(reinterpret_cast<const float4 *>(p) + 1);
             v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
             v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
         } else {
-            const uint4 r = *reinterpret_cast<const uint4 *>(p);
+            const uint4 r = gld<COH>(reinterpret_cast<const uint4 *>(p));
             const unsigned w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -662,7 +709,7 @@ __device__ __forceinline__ void ld_seg(const T *p, int n, float (&v)[SX]) {
         return;
     }
 #pragma unroll
-    for (int j = 0; j < SX; ++j) v[j] = j < n ? Stor<T>::ld(p, j) : 0.f;
+    for (int j = 0; j < SX; ++j) v[j] = j < n ? gld_elem<COH>(p, j) : 0.f;
 }
 
 template <typename T>
@@ -725,17 +772,27 @@ __device__ __forceinline__ void st_mask8(uint8_t *p, int n, unsigned long long v
 // Seven resident CTAs per SM (<= 72 registers) while the staged halo allows
 // it; the selective-convolution variant needs more registers.
 template <int R, bool THIN>
-constexpr int min_blocks() { return R > 12 ? 5 : R > 8 ? 6 : THIN || R == 1 ? 5 : 7; }
+constexpr int min_blocks() { return disc_min_blocks(R, THIN); }
+// A wide disc tile (8 x 8 blocks, 64 accumulators per thread) fits four
+// CTAs per SM up to R = 8 (its staged tile is 50 KB), three beyond.
+template <typename Op, bool THIN>
+constexpr int op_min_blocks() { return Op::kWide ? (Op::kR > 8 ? 3 : 4) : min_blocks<Op::kR, THIN>(); }
 
-// One 64 x 64 output tile (tbx, tby) of a half-iteration, run by the whole
-// CTA; the kernels below call it once per CTA.
-template <typename T, bool THIN, typename Op, bool FWD>
+// One output tile (tbx, tby) of a half-iteration (Op::kTX x Op::kTY, blocks
+// of Op::kSY x SX), run by the whole CTA; the kernels below call it once per
+// CTA or per work item.
+template <typename T, bool THIN, typename Op, bool FWD, bool COH = false>
 __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                                           long long q_pitch, int tbx, int tby) {
     constexpr int R = Op::kR;
+    constexpr int GTX = Op::kTX, GTY = Op::kTY, GSY = Op::kSY;
+    constexpr int NBX = GTX / SX;  // block columns of the tile
+    static_assert(NBX % 8 == 0 && (GTY / GSY) % 4 == 0, "a warp covers 8 x 4 blocks");
+    static_assert(NBX * (GTY / GSY) == 128, "one block per thread");
+    static_assert(!(THIN && Op::kWide), "selective convolution uses the default tile (tile flags)");
     using G = typename Op::Geom;
     extern __shared__ float sm[];
-    const int x0 = tbx * TX, y0 = tby * TY;
+    const int x0 = tbx * GTX, y0 = tby * GTY;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned used = 0;
     bool tile_any = false;  // a pixel of this thread's blocks stays active
@@ -744,21 +801,24 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + tby * a.tiles_x + tbx : nullptr;
     if (tflag && !a.full && *tflag == 0) return;
     if (FWD)
-        stage_halo<T, G::NR, G::NU, G::HP>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
+        stage_halo<T, G::NR, G::NU, G::HP, COH>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
                                     threadIdx.x);
     else
-        stage_halo<float, G::NR, G::NU, G::HP>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
+        stage_halo<float, G::NR, G::NU, G::HP, COH>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
                                         threadIdx.x);
     {
         // The epilogue reads f (forward) or u (adjoint) at the tile's pixels:
         // start moving those rows into L2 now, while the halo lands and the
-        // blocks are summed.  Thread t covers 128 bytes of row t / L.
-        constexpr int L = (TX * (int)sizeof(T) + 127) / 128;  // 128-byte lines per tile row
-        const int y = y0 + threadIdx.x / L, x = x0 + (threadIdx.x % L) * (128 / (int)sizeof(T));
-        if (threadIdx.x < TY * L && y < a.H && x < a.W) {
-            const T *p = FWD ? (const T *)a.f + (long long)y * a.f_pitch + x
-                             : (const T *)a.u_in + (long long)y * a.in_pitch + x;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        // blocks are summed.  Entry e covers 128 bytes of tile row e / L.
+        constexpr int L = (GTX * (int)sizeof(T) + 127) / 128;  // 128-byte lines per tile row
+#pragma unroll
+        for (int e = threadIdx.x; e < GTY * L; e += 128) {
+            const int y = y0 + e / L, x = x0 + (e % L) * (128 / (int)sizeof(T));
+            if (y < a.H && x < a.W) {
+                const T *p = FWD ? (const T *)a.f + (long long)y * a.f_pitch + x
+                                 : (const T *)a.u_in + (long long)y * a.in_pitch + x;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+            }
         }
     }
     cp_async_wait_all();
@@ -767,20 +827,20 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         Op::template prepass<FWD>(sm, sm + G::NR * G::HP, prm);
         __syncthreads();
     }
-    // Natural block of this thread: warp w covers block rows 4w .. 4w + 3,
-    // lane = 8 (x) x 4 (y) blocks, so the 8 lanes of a 16-byte load phase
-    // share a block row.
-    const int nbx = lane & 7, nby = wid * 4 + (lane >> 3);
+    // Natural block of this thread: a warp covers 8 (x) x 4 (y) blocks -- the
+    // 8 lanes of a 16-byte load phase share a block row -- and the warps tile
+    // the NBX x (GTY / GSY) blocks row group by row group.
+    const int nbx = (lane & 7) + 8 * (wid % (NBX / 8)), nby = wid / (NBX / 8) * 4 + (lane >> 3);
     // Selective convolution: compact the blocks with at least one pixel used
     // this iteration (warp ballot + prefix over the warps) and convolve only
     // those; warps left without blocks retire early.
-    int n_active = TX / SX * TY / SY;
-    __shared__ int blist[TX / SX * TY / SY];
+    int n_active = GTX / SX * GTY / GSY;
+    __shared__ int blist[GTX / SX * GTY / GSY];
     __shared__ int wcount[4];
     if (THIN && !a.full) {
         bool any = false;
-        for (int i = 0; i < SY; ++i) {
-            const int y = y0 + nby * SY + i, x = x0 + nbx * SX;
+        for (int i = 0; i < GSY; ++i) {
+            const int y = y0 + nby * GSY + i, x = x0 + nbx * SX;
             if (y < a.H && x < a.W) {
                 const uint8_t *mrow = a.mask_in + (long long)y * a.mi_pitch + x;
                 if (x + SX <= a.W && ((reinterpret_cast<uintptr_t>(mrow) & 7) == 0)) {
@@ -796,7 +856,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         int off = 0;
         for (int k = 0; k < wid; ++k) off += wcount[k];
         n_active = wcount[0] + wcount[1] + wcount[2] + wcount[3];
-        if (any) blist[off + __popc(bal & ((1u << lane) - 1u))] = nby * (TX / SX) + nbx;
+        if (any) blist[off + __popc(bal & ((1u << lane) - 1u))] = nby * (GTX / SX) + nbx;
         __syncthreads();
     }
 #pragma unroll 1
@@ -804,18 +864,18 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         int bx = nbx, by = nby;
         if (THIN && !a.full) {
             const int b = blist[e];
-            bx = b % (TX / SX);
-            by = b / (TX / SX);
+            bx = b % (GTX / SX);
+            by = b / (GTX / SX);
         }
-        const int xb = x0 + bx * SX, yb = y0 + by * SY;
-        float acc[SY][SX];
-        Op::template block<FWD>(sm, by * SY, bx, acc, prm);
+        const int xb = x0 + bx * SX, yb = y0 + by * GSY;
+        float acc[GSY][SX];
+        Op::template block<FWD>(sm, by * GSY, bx, acc, prm);
         // exact transpose: band pixels of border tiles take A^T q from the band plane
         const bool band = !FWD && a.fold_ct &&
-                          (x0 < a.fold_rx || x0 + TX > a.W - a.fold_rx || y0 < a.fold_ry || y0 + TY > a.H - a.fold_ry);
+                          (x0 < a.fold_rx || x0 + GTX > a.W - a.fold_rx || y0 < a.fold_ry || y0 + GTY > a.H - a.fold_ry);
         if (band) {
 #pragma unroll
-            for (int i = 0; i < SY; ++i) {
+            for (int i = 0; i < GSY; ++i) {
                 const int y = yb + i;
 #pragma unroll
                 for (int j = 0; j < SX; ++j) {
@@ -831,7 +891,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         if (!THIN) {
             const int n = min(SX, a.W - xb);
 #pragma unroll
-            for (int i = 0; i < SY; ++i) {
+            for (int i = 0; i < GSY; ++i) {
                 const int y = yb + i;
                 if (y >= a.H || n <= 0) break;
                 float e[SX], o[SX];
@@ -842,7 +902,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
                         o[j] = rl_ratio(e[j], Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
                     st_seg<float>(qplane + (long long)y * q_pitch + xb, n, o);
                 } else {
-                    ld_seg<T>((const T *)a.u_in + (long long)y * a.in_pitch + xb, n, e);
+                    ld_seg<T, COH>((const T *)a.u_in + (long long)y * a.in_pitch + xb, n, e);
 #pragma unroll
                     for (int j = 0; j < SX; ++j)
                         o[j] = e[j] * (Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
@@ -855,7 +915,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         // time: mask bytes as one 8-byte access, f / u and u' as 16-byte ones
         const int n = min(SX, a.W - xb);
 #pragma unroll
-        for (int i = 0; i < SY; ++i) {
+        for (int i = 0; i < GSY; ++i) {
             const int y = yb + i;
             if (y >= a.H || n <= 0) break;
             const unsigned long long ones = 0x0101010101010101ull;
@@ -878,7 +938,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
                 }
             } else {
                 float uv[SX], o[SX];
-                ld_seg<T>((const T *)a.u_in + (long long)y * a.in_pitch + xb, n, uv);
+                ld_seg<T, COH>((const T *)a.u_in + (long long)y * a.in_pitch + xb, n, uv);
                 unsigned long long mo = 0;
 #pragma unroll
                 for (int j = 0; j < SX; ++j) {
@@ -913,7 +973,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
 }
 
 template <typename T, bool THIN, typename Op, bool FWD>
-__global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>())
+__global__ void __launch_bounds__(128, op_min_blocks<Op, THIN>())
     k_disc_half(const __grid_constant__ IterArgs a, const __grid_constant__ typename Op::Params prm, float *qplane,
                 long long q_pitch) {
     // Programmatic dependent launch: this grid may start while the previous
@@ -930,7 +990,7 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, THIN>())
 // ones (phase 1).  Jobs of one launch share the block operation; FP32
 // storage, no thinning.
 template <typename Op, bool FWD>
-__global__ void __launch_bounds__(128, min_blocks<Op::kR, false>())
+__global__ void __launch_bounds__(128, op_min_blocks<Op, false>())
     k_disc_half_tiles(const TileJob *jobs, const int2 *items, int phase,
                       const __grid_constant__ typename Op::Params prm) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -938,8 +998,117 @@ __global__ void __launch_bounds__(128, min_blocks<Op::kR, false>())
     const int2 it = items[blockIdx.x];
     const TileJob &job = jobs[it.x];
     const IterArgs &a = job.a[phase];
-    const int tiles_x = (a.W + TX - 1) / TX;
+    const int tiles_x = (a.W + Op::kTX - 1) / Op::kTX;
     half_tile<float, false, Op, FWD>(a, prm, job.qplane, job.q_pitch, it.y % tiles_x, it.y / tiles_x);
+}
+
+// ---- persistent form --------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until *w >= need (a neighbour tile has finished the previous half).
+// Gives up when another CTA reported an error or after wait_ns, which it
+// reports; returns whether the wait succeeded.
+__device__ __forceinline__ bool wait_tile(const int *w, int need, int *status, unsigned long long wait_ns) {
+    if (ld_acquire_gpu(w) >= need) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        __nanosleep(64);
+        if (ld_acquire_gpu(w) >= need) return true;
+        if (*(volatile int *)status != 0) return false;
+        if (global_ns() - t0 > wait_ns) {
+            atomicCAS(status, 0, 1);
+            return false;
+        }
+    }
+}
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(128, op_min_blocks<Op, false>())
+    k_disc_persist(const __grid_constant__ PersistArgs p, const __grid_constant__ typename Op::Params prm) {
+    __shared__ int s_item;
+    const int n_tiles = p.tiles_x * p.tiles_y;
+    const int n_items = 2 * p.K * n_tiles;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.ticket, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int hk = item / n_tiles;  // half index: 2 k (forward) or 2 k + 1 (adjoint)
+        const int t = item - hk * n_tiles;
+        const int tbx = t % p.tiles_x, tby = t / p.tiles_x;
+        // the previous half must be complete on the tile and its 8 neighbours
+        // (halo <= 16 < 64 pixels): threads 0..8 wait for one tile each
+        bool ok = true;
+        if (hk > 0 && threadIdx.x < 9) {
+            const int nx = tbx + (int)threadIdx.x % 3 - 1, ny = tby + (int)threadIdx.x / 3 - 1;
+            if (nx >= 0 && nx < p.tiles_x && ny >= 0 && ny < p.tiles_y)
+                ok = wait_tile(p.progress + ny * p.tiles_x + nx, hk, p.status, p.wait_ns);
+        }
+        if (!__syncthreads_and(ok)) break;
+        const int k = hk >> 1;
+        const IterArgs &a = p.a[(k > 0) + 2 * (k == p.K - 1)];
+        if ((hk & 1) == 0)
+            half_tile<T, false, Op, true, true>(a, prm, p.qplane, p.q_pitch, tbx, tby);
+        else
+            half_tile<T, false, Op, false, true>(a, prm, p.qplane, p.q_pitch, tbx, tby);
+        // every store of the tile is issued; publish them, then the progress
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(p.progress + t, hk + 1);
+        }
+    }
+}
+
+template <typename Op, typename T>
+cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cudaStream_t s) {
+    constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
+    // tiles of this op (the host sized progress for 64 x 64 tiles, at least as many)
+    p.tiles_x = (p.a[0].W + Op::kTX - 1) / Op::kTX;
+    p.tiles_y = (p.a[0].H + Op::kTY - 1) / Op::kTY;
+    cudaError_t e = ensure_smem<k_disc_persist<T, Op>>(smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disc_persist<T, Op>, 128, smem)) != cudaSuccess)
+        return e;
+    if (occ < 1) return cudaErrorNotSupported;
+    const long long n_items = 2LL * p.K * p.tiles_x * p.tiles_y;
+    const long long grid = std::min<long long>((long long)occ * sms, n_items);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: waits between them cannot deadlock
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_disc_persist<T, Op>, p, prm);
+}
+
+template <typename Op>
+cudaError_t launch_persist(const PersistArgs &p, const typename Op::Params &prm, int storage, cudaStream_t s) {
+    switch (storage) {
+    case ST_F32: return launch_persist_t<Op, float>(p, prm, s);
+    case ST_BF16: return launch_persist_t<Op, __nv_bfloat16>(p, prm, s);
+    case ST_F16: return launch_persist_t<Op, __half>(p, prm, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename Op, typename T, bool THIN>
@@ -950,7 +1119,7 @@ cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float 
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((a.W + TX - 1) / TX, (a.H + TY - 1) / TY);
+    cfg.gridDim = dim3((a.W + Op::kTX - 1) / Op::kTX, (a.H + Op::kTY - 1) / Op::kTY);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -989,19 +1158,24 @@ cudaError_t launch_op_tiles(const TileJob *jobs, const int2 *items, int n_items,
     return e;
 }
 
-template <typename Op>
-cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int storage, bool thin,
-                      float *qplane, long long q_pitch, cudaStream_t s) {
+template <typename Op, bool THIN>
+cudaError_t launch_op_t(const IterArgs &a, const typename Op::Params &prm, int storage, float *qplane,
+                        long long q_pitch, cudaStream_t s) {
     switch (storage) {
-    case ST_F32: return thin ? launch_one<Op, float, true>(a, prm, qplane, q_pitch, s)
-                             : launch_one<Op, float, false>(a, prm, qplane, q_pitch, s);
-    case ST_BF16: return thin ? launch_one<Op, __nv_bfloat16, true>(a, prm, qplane, q_pitch, s)
-                              : launch_one<Op, __nv_bfloat16, false>(a, prm, qplane, q_pitch, s);
-    case ST_F16: return thin ? launch_one<Op, __half, true>(a, prm, qplane, q_pitch, s)
-                             : launch_one<Op, __half, false>(a, prm, qplane, q_pitch, s);
+    case ST_F32: return launch_one<Op, float, THIN>(a, prm, qplane, q_pitch, s);
+    case ST_BF16: return launch_one<Op, __nv_bfloat16, THIN>(a, prm, qplane, q_pitch, s);
+    case ST_F16: return launch_one<Op, __half, THIN>(a, prm, qplane, q_pitch, s);
     }
     return cudaErrorInvalidValue;
 }
+
+template <typename Op>
+cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int storage, bool thin,
+                      float *qplane, long long q_pitch, cudaStream_t s) {
+    return thin ? launch_op_t<Op, true>(a, prm, storage, qplane, q_pitch, s)
+                : launch_op_t<Op, false>(a, prm, storage, qplane, q_pitch, s);
+}
+
 
 }  // namespace disc
 }  // namespace rl
@@ -1017,6 +1191,9 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
     cudaError_t launch_disc_tiles_r##R(const TileJob *jobs, const int2 *items, int n_items,  \
                                        int phase, cudaStream_t s) {                          \
         return disc::launch_op_tiles<disc::DiscOp<R>>(jobs, items, n_items, phase, {}, s);   \
+    }                                                                                        \
+    cudaError_t launch_disc_persist_r##R(const PersistArgs &p, int storage, cudaStream_t s) { \
+        return disc::launch_persist<disc::DiscOp<R>>(p, {}, storage, s);                     \
     }                                                                                        \
     }
 

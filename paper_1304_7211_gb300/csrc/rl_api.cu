@@ -23,6 +23,7 @@ using rl::IterArgs;
 
 struct rl_ctx {
     int device = 0;
+    int sms = 0;  // multiprocessors of the device
     cudaStream_t stream = nullptr;
     int storage = RL_STORAGE_F32;
     int boundary = RL_BOUNDARY_MIRROR;
@@ -79,6 +80,10 @@ struct rl_ctx {
     size_t q_px = 0;
     int *tflags = nullptr;    // per-tile activity of the disc path
     size_t tflags_n = 0;
+    // persistent disc kernel: per-tile progress, work ticket and status word
+    int *pscratch = nullptr;
+    size_t pscratch_bytes = 0;
+    const int *pstatus = nullptr;  // status word of the last persistent launch, or NULL
     void *tbuf[2] = {nullptr, nullptr};  // transposed f and u (motion along y)
     size_t tbuf_bytes = 0;
     void *tsched = nullptr;              // transposed schedule / mask bytes
@@ -195,6 +200,7 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
         return RL_ERR_OOM;
     }
     ctx->device = c.device;
+    ctx->sms = prop.multiProcessorCount;
     ctx->stream = (cudaStream_t)c.stream;
     ctx->storage = c.storage;
     ctx->boundary = c.boundary;
@@ -246,6 +252,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     cudaFree(ctx->ctplane);
     cudaFree(ctx->zplane);
     cudaFree(ctx->tflags);
+    cudaFree(ctx->pscratch);
     cudaFree(ctx->tbuf[0]);
     cudaFree(ctx->tbuf[1]);
     cudaFree(ctx->tsched);
@@ -775,6 +782,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         }
     }
     void *work = ctx->ubuf[0];
+    ctx->pstatus = nullptr;
     auto args_for = [&](int k) {
         IterArgs b = a;
         const bool last = k == K - 1;
@@ -809,6 +817,43 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         ctx->launches += 2;
         return RL_OK;
     };
+    // Plain disc: every iteration in one persistent launch (tiles advance as
+    // their neighbourhood allows, no barrier between the halves) when the
+    // image has enough tiles to keep the resident CTAs busy while some wait:
+    // at about one tile per CTA slot the two launches per iteration are
+    // faster (measured: 41.5 vs 38.5 us/it for the disc r = 8 at 2048^2,
+    // 127 vs 137 us/it for r = 12 at 4096^2).
+    const int tx = (W + rl::disc_tile() - 1) / rl::disc_tile(), ty = (H + rl::disc_tile() - 1) / rl::disc_tile();
+    const long long slots = (long long)ctx->sms * rl::disc_min_blocks(R, false);
+    const bool persist_pays = 4LL * tx * ty >= 5LL * slots;  // at least 1.25 tiles per slot
+    if (op == OP_DISC && !thin && !a.fold_ct && !(ctx->flags & RL_FLAG_PER_ITERATION) &&
+        (persist_pays || (ctx->flags & RL_FLAG_PERSISTENT))) {
+        const size_t n = (size_t)tx * ty + 2;  // progress per tile, ticket, status
+        rl_status st = grow(ctx, (void **)&ctx->pscratch, &ctx->pscratch_bytes, n * sizeof(int),
+                            "rl_iterate: tile progress");
+        if (st != RL_OK) return st;
+        CK(cudaMemsetAsync(ctx->pscratch, 0, n * sizeof(int), ctx->stream), "rl_iterate: tile progress");
+        rl::PersistArgs pa;
+        memset(&pa, 0, sizeof pa);
+        pa.a[0] = args_for(0);
+        pa.a[1] = args_for(K > 2 ? 1 : 0);
+        pa.a[2] = args_for(0);
+        pa.a[3] = args_for(K - 1);
+        pa.qplane = ctx->qplane;
+        pa.q_pitch = sp;
+        pa.K = K;
+        pa.tiles_x = tx;
+        pa.tiles_y = ty;
+        pa.progress = ctx->pscratch;
+        pa.ticket = (unsigned *)(ctx->pscratch + tx * ty);
+        pa.status = ctx->pscratch + tx * ty + 1;
+        pa.wait_ns = 2000000000ull;  // 2 s for one neighbour tile: only a fault gets near it
+        const cudaError_t e = rl::launch_disc_persist(pa, ctx->storage, R, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: persistent launch");
+        ctx->pstatus = pa.status;
+        ctx->launches += 1;
+        return RL_OK;
+    }
     // iteration 0 reads the start image; the middle iterations repeat with
     // period G (in place; thinning epochs of reset_period) and are replayed
     // from a CUDA graph; the last one (no thinning) writes the caller's buffer
@@ -1151,6 +1196,13 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
     } else if (staged) {
         CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: sync");
     }
+    if ((stats || staged) && ctx->pstatus) {
+        // the stream is synchronised: did a persistent launch give up waiting?
+        int pst = 0;
+        CK(cudaMemcpy(&pst, ctx->pstatus, sizeof pst, cudaMemcpyDeviceToHost), "rl_iterate: status");
+        if (pst != 0)
+            return fail(ctx, RL_ERR_TIMEOUT, "rl_iterate: the persistent disc kernel gave up waiting for a tile");
+    }
     CK(cudaGetLastError(), "rl_iterate");
     ctx->err.clear();
     return RL_OK;
@@ -1319,4 +1371,65 @@ extern "C" rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch) {
     cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_get_mask");
     return RL_OK;
+}
+
+// Failure detection of the persistent disc kernel without a GPU fault: a
+// small launch whose ticket counter starts past the forward half of its only
+// iteration, so every adjoint item waits for neighbours that never finish.
+// Each wait gives up after wait_ms, the kernel records status 1 and every CTA
+// returns; the context stays usable.
+extern "C" rl_status rl_selftest_wait_timeout(int device, int wait_ms) {
+    if (wait_ms < 1 || wait_ms > 10000) return RL_ERR_INVALID_ARG;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RL_ERR_CUDA;
+    }
+    const int W = 128, H = 128, tiles = (W / rl::disc_tile()) * (H / rl::disc_tile());
+    float *buf = nullptr;  // f, work u, out, q
+    int *scratch = nullptr;
+    cudaStream_t s = nullptr;
+    rl_status st = RL_ERR_CUDA;
+    cudaError_t e = cudaMalloc(&buf, 4 * sizeof(float) * W * H);
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, (tiles + 2) * sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 4 * sizeof(float) * W * H, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, (tiles + 2) * sizeof(int), s);
+    const unsigned first = (unsigned)tiles;  // the forward half of iteration 0 is never handed out
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + tiles, &first, sizeof first, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        rl::PersistArgs p;
+        memset(&p, 0, sizeof p);
+        IterArgs a;
+        memset(&a, 0, sizeof a);
+        a.f = buf;
+        a.u_in = buf;
+        a.u_out = buf + 2 * W * H;
+        a.W = W;
+        a.H = H;
+        a.f_pitch = a.in_pitch = a.out_pitch = W;
+        a.ax = a.bx = a.ay = a.by = 2;
+        a.weight = 1.f / 13.f;
+        for (int i = 0; i < 4; ++i) p.a[i] = a;
+        p.qplane = buf + 3 * W * H;
+        p.q_pitch = W;
+        p.K = 1;
+        p.tiles_x = W / rl::disc_tile();
+        p.tiles_y = H / rl::disc_tile();
+        p.progress = scratch;
+        p.ticket = (unsigned *)(scratch + tiles);
+        p.status = scratch + tiles + 1;
+        p.wait_ns = (unsigned long long)wait_ms * 1000000ull;
+        e = rl::launch_disc_persist(p, rl::ST_F32, 2, s);
+    }
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, scratch + tiles + 1, sizeof status, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) st = status == 1 ? RL_ERR_TIMEOUT : RL_ERR_STATE;
+    (void)cudaGetLastError();
+    if (s) cudaStreamDestroy(s);
+    cudaFree(buf);
+    cudaFree(scratch);
+    cudaSetDevice(prev);
+    return st;
 }

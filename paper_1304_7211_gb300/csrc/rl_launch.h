@@ -61,6 +61,11 @@ cudaError_t launch_tile_f16(const IterArgs &a, bool thin, int mode, TileShape ts
 // radius): the defocus disc of radius 1..16 with compile-time runs.  One RL
 // iteration = two launches sharing the library-owned FP32 q plane.
 constexpr int kDiscMaxRadius = 16;
+constexpr int disc_tile() { return 64; }  // output tile edge of the two-half kernels
+// Resident CTAs per SM the two-half kernels are compiled for (register cap of
+// their launch bounds; the staged tile fits as many): seven up to R = 8, six
+// up to 12, five beyond, five with selective convolution or R = 1.
+constexpr int disc_min_blocks(int R, bool thin) { return R > 12 ? 5 : R > 8 ? 6 : thin || R == 1 ? 5 : 7; }
 cudaError_t launch_disc(const IterArgs &a, int storage, bool thin, int radius, float *qplane,
                         long long q_pitch, cudaStream_t s);
 #define RL_DECLARE_DISC_R(R)                                                                 \
@@ -93,6 +98,39 @@ RL_DECLARE_TILES_R(5) RL_DECLARE_TILES_R(6) RL_DECLARE_TILES_R(7) RL_DECLARE_TIL
 RL_DECLARE_TILES_R(9) RL_DECLARE_TILES_R(10) RL_DECLARE_TILES_R(11) RL_DECLARE_TILES_R(12)
 RL_DECLARE_TILES_R(13) RL_DECLARE_TILES_R(14) RL_DECLARE_TILES_R(15) RL_DECLARE_TILES_R(16)
 #undef RL_DECLARE_TILES_R
+
+// Persistent form of the disc halves: all K iterations of one image in one
+// cooperative launch.  Work items (iteration k, half, tile) are handed out in
+// that order by a ticket counter; an item starts once the 3 x 3 tiles around
+// its tile have finished the previous half (per-tile progress counters,
+// release / acquire at GPU scope), so no grid-wide barrier separates the
+// halves and one tile's staging overlaps other tiles' sums.  a[] holds the
+// arguments of the four kinds of iteration, index (k > 0) + 2 (k == K - 1):
+// the first reads the start image, the last writes the caller's buffer, the
+// others work in place on a library u plane.  progress, ticket and status
+// are zeroed before the launch; a wait longer than wait_ns sets status to 1
+// and every CTA returns.  No thinning, no transpose band.
+struct PersistArgs {
+    IterArgs a[4];
+    float *qplane;
+    long long q_pitch;
+    int K;
+    int tiles_x, tiles_y;
+    int *progress;             // per tile: halves completed
+    unsigned *ticket;          // next work item
+    int *status;               // 0, or 1 when a wait gave up
+    unsigned long long wait_ns;
+};
+// Launch with a grid of every co-resident CTA (occupancy x SMs); returns
+// cudaErrorNotSupported when the radius has no persistent kernel.
+cudaError_t launch_disc_persist(const PersistArgs &p, int storage, int radius, cudaStream_t s);
+#define RL_DECLARE_PERSIST_R(R) \
+    cudaError_t launch_disc_persist_r##R(const PersistArgs &p, int storage, cudaStream_t s);
+RL_DECLARE_PERSIST_R(1) RL_DECLARE_PERSIST_R(2) RL_DECLARE_PERSIST_R(3) RL_DECLARE_PERSIST_R(4)
+RL_DECLARE_PERSIST_R(5) RL_DECLARE_PERSIST_R(6) RL_DECLARE_PERSIST_R(7) RL_DECLARE_PERSIST_R(8)
+RL_DECLARE_PERSIST_R(9) RL_DECLARE_PERSIST_R(10) RL_DECLARE_PERSIST_R(11) RL_DECLARE_PERSIST_R(12)
+RL_DECLARE_PERSIST_R(13) RL_DECLARE_PERSIST_R(14) RL_DECLARE_PERSIST_R(15) RL_DECLARE_PERSIST_R(16)
+#undef RL_DECLARE_PERSIST_R
 
 // Register-blocked uniform square box (2R + 1)^2, R = 1..16 (k_box_*.cu): the
 // disc's run sums with every run at half-width R.

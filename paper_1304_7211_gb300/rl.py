@@ -51,6 +51,7 @@ class rl_thinning(ctypes.Structure):
 
 RL_FLAG_PER_ITERATION = 1
 RL_FLAG_ADJOINT_TRANSPOSE = 2
+RL_FLAG_PERSISTENT = 4
 ADJOINT = {"padflip": 0, "transpose": RL_FLAG_ADJOINT_TRANSPOSE}
 
 
@@ -87,7 +88,7 @@ _lib = None
 EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error", "rl_version",
            "rl_get_mask", "rl_motion_x_noalloc", "rl_batch_create", "rl_batch_submit",
            "rl_batch_query", "rl_batch_wait", "rl_batch_sync", "rl_batch_destroy",
-           "rl_batch_last_error", "rl_iterate_tiles")
+           "rl_batch_last_error", "rl_iterate_tiles", "rl_selftest_wait_timeout")
 RL_NOALLOC_MAX_PIXELS = 4194304
 
 
@@ -136,6 +137,8 @@ def load() -> ctypes.CDLL:
     lib.rl_motion_x_noalloc.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                         ctypes.c_char_p, ctypes.c_int]
+    lib.rl_selftest_wait_timeout.restype = ctypes.c_int
+    lib.rl_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_int]
     _lib = lib
     return lib
 
