@@ -20,8 +20,11 @@ sample of the same workload and prints the same JSON line.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -38,6 +41,81 @@ SIZE = 2048
 ITERS = 200
 WORKLOAD = "plain RL 2048x2048 fp32, PSFs motion-x 31 / motion-y 31 / disc r8, 200 it each"
 L2_FLUSH_BYTES = 512 << 20
+CPU_ITERS = 3          # oracle iterations per PSF in the CPU baseline sample
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_plain_2048.json")
+
+
+def source_sha() -> str:
+    """Hash of every CUDA source and the ABI header: a DRAM-traffic capture
+    counts for this build only if it was taken on the same sources."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1304_7211_gb300", "csrc", "*")))
+    for path in files + [os.path.join(ROOT, "include", "rl.h")]:
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_key(name: str) -> str:
+    """Short kernel name from ncu's demangled one: template arguments kept,
+    namespaces and the parameter list dropped."""
+    name = name.split("(")[0].replace("void ", "").strip()
+    return re.sub(r"\brl::(disc::|mtb::)?", "", name)
+
+
+def ingest_ncu(csv_path: str, out_path: str, workload: str, command: str) -> dict:
+    """Per-kernel launches, DRAM bytes and device time per launch from an ncu
+    CSV (``--csv --page raw``: one row per launch, a row of units under the
+    header) of gpu__time_duration.sum and dram__bytes_{read,write}.sum,
+    tagged with the source hash of this build."""
+    import csv
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
+             "nsecond": 1e-9, "ns": 1e-9, "usecond": 1e-6, "us": 1e-6, "msecond": 1e-3, "ms": 1e-3,
+             "second": 1.0, "s": 1.0}
+    with open(csv_path) as fh:
+        rows = list(csv.reader(ln for ln in fh if ln.startswith('"')))
+    hdr, units = rows[0], rows[1]
+    col = {n: i for i, n in enumerate(hdr)}
+    name_col = col.get("Kernel Name", col.get("Function Name"))
+    kernels = {}
+    for r in rows[2:]:
+        def val(metric):
+            i = col.get(metric)
+            if i is None or not r[i]:
+                return 0.0
+            return float(r[i].replace(",", "")) * scale.get(units[i], 1.0)
+        k = kernel_key(r[name_col])
+        e = kernels.setdefault(k, {"launches": 0, "dram_bytes": 0.0, "seconds": 0.0})
+        e["launches"] += 1
+        e["dram_bytes"] += val("dram__bytes_read.sum") + val("dram__bytes_write.sum")
+        e["seconds"] += val("gpu__time_duration.sum")
+    out = {"build_sha": source_sha(), "workload": workload, "command": command,
+           "kernels": {k: {"launches": e["launches"],
+                           "dram_bytes_per_launch": e["dram_bytes"] / e["launches"],
+                           "us_per_launch": 1e6 * e["seconds"] / e["launches"]}
+                       for k, e in sorted(kernels.items())}}
+    with open(out_path, "w") as fh:
+        json.dump(out, fh, indent=1)
+        fh.write("\n")
+    return out
+
+
+def measured_traffic():
+    """The DRAM-traffic capture of this build (profiles/), or None when the
+    sources changed since it was taken."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    d = json.load(open(TRAFFIC_FILE))
+    return d if d.get("build_sha") == source_sha() else None
+
+
+def traffic_of(cap, pred):
+    """Summed DRAM bytes per launch of the captured kernels matching pred."""
+    if cap is None:
+        return None
+    ks = [v for k, v in cap["kernels"].items() if pred(k)]
+    return sum(v["dram_bytes_per_launch"] for v in ks) if ks else None
 
 
 def whole_job_rate(units_per_rank: float, seconds: float, world_size: int, device=None) -> tuple:
@@ -125,53 +203,90 @@ def make_inputs():
     return out
 
 
-def cpu_baseline_run(inputs, budget_s: float = 20.0):
-    """Time the FP64 oracle (as it stands) on the host cores on a bounded
-    sample: the full 2048^2 image of each PSF for a few iterations."""
+def oracle_sample(inputs, its=CPU_ITERS):
+    """The FP64 oracle, as it stands, on the full 2048^2 image of each PSF for
+    `its` iterations: (pixel-iterations, seconds, per-PSF notes)."""
     import numpy as np
     import oracle
     oracle.build()
-    px_it = 0
-    t_total = 0.0
-    per = []
+    px_it, t_total, per = 0, 0.0, []
     for spec, f32 in inputs:
         t = spec.dense()
         psf = oracle.psf_dense(t, t.shape[1] // 2, t.shape[0] // 2)
         f64 = f32.astype(np.float64)
-        its = 2
         t0 = time.perf_counter()
         oracle.rl(f64, psf, its)
         dt = time.perf_counter() - t0
         t_total += dt
         px_it += f64.size * its
-        per.append(f"{spec.name}:{its}it/{dt:.1f}s")
+        per.append(f"{spec.name}:{its}it/{dt:.2f}s")
+    return px_it, t_total, per
+
+
+def _single_thread_sample(inputs) -> dict:
+    """The same sample in a fresh process limited to one OpenMP thread."""
+    import numpy as np
+    with tempfile.TemporaryDirectory() as td:
+        names = []
+        for i, (spec, f32) in enumerate(inputs):
+            np.save(os.path.join(td, f"f{i}.npy"), f32)
+            names.append(spec.name)
+        code = (
+            "import json, sys, numpy as np; sys.path.insert(0, %r)\n"
+            "import bench\n"
+            "from paper_1304_7211_gb300 import synth\n"
+            "specs = {s.name: s for s in synth.CONFIG2_PSFS}\n"
+            "inp = [(specs[n], np.load(%r + '/f%%d.npy' %% i)) for i, n in enumerate(%r)]\n"
+            "print(json.dumps(bench.oracle_sample(inp)))\n" % (ROOT, td, names))
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=600)
+        px_it, secs, per = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": px_it / secs / 1e6, "unit": UNIT, "cores": 1, "seconds": secs,
+            "sample": f"full 2048x2048 image, {CPU_ITERS} iterations per PSF ({', '.join(per)})"}
+
+
+def cpu_baseline_run(inputs, single_thread: bool = True):
+    """Time the FP64 oracle (as it stands) on the host cores on a bounded
+    sample: the full 2048^2 image of each PSF for CPU_ITERS iterations, with
+    every core (OpenMP over rows) and, in a fresh process, with one."""
+    px_it, secs, per = oracle_sample(inputs)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": px_it / t_total / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"full 2048x2048 image, 2 iterations per PSF ({', '.join(per)}); "
-                      f"FP64 direct summation, OpenMP over rows"}
+    d = {"value": px_it / secs / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+         "seconds": secs,
+         "sample": f"full 2048x2048 image, {CPU_ITERS} iterations per PSF ({', '.join(per)}); "
+                   f"FP64 direct summation, OpenMP over rows"}
+    if single_thread:
+        try:
+            d["single_thread"] = _single_thread_sample(inputs)
+        except Exception as e:  # reported, not fatal: the all-core figure stands
+            d["single_thread"] = {"error": str(e)[:200]}
+    return d
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
+    # Each step is a bounded sample of the workload: the full 2048^2 image of
+    # every PSF for CPU_ITERS iterations (not the 200 of the GPU step), timed
+    # as it runs; the rate is over the sample's own pixel-iterations.
     inputs = make_inputs()
-    vals = []
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state worth the CPU time
-    cb = None
+    oracle_sample(inputs, its=1)  # warm-up: builds and loads the oracle
+    secs, px = [], 0
     for _ in range(args.steps):
-        cb = cpu_baseline_run(inputs)
-        vals.append(cb["value"])
-    v = statistics.median(vals)
-    cb["value"] = v
-    px_step = 3 * SIZE * SIZE * ITERS
+        px, t, per = oracle_sample(inputs)
+        secs.append(t)
+    v = px * len(secs) / sum(secs) / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"full 2048x2048 image, {CPU_ITERS} iterations per PSF per step ({', '.join(per)}); "
+              f"FP64 direct summation, OpenMP over rows")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": px_step / (v * 1e6) * 1e3, "higher_is_better": True,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (CPU oracle, bounded sample)", "size": SIZE,
-                       "iterations": ITERS},
-            "cpu_baseline": cb,
+            "config": {"workload": WORKLOAD + f" (CPU oracle; a step is the {CPU_ITERS}-iteration sample)",
+                       "size": SIZE, "iterations": CPU_ITERS},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -395,6 +510,79 @@ def thinned_run(local, size=4096, iters=300, oracle_size=384):
             "oracle_cpu_s": oracle_s, "rows": rows}
 
 
+def solve_roofline(spec, ms_solve, launches, pk, pk_kind, sms, cap) -> dict:
+    """Roofline of one 200-iteration 2048^2 solve's kernel, from its live
+    CUDA-event time.  Disc (span path): 2 (2r + 1) run-end additions per pixel
+    per convolution (Sec. 3, generic box filter), two convolutions, plus the
+    ratio, the update and two scalings, against the FP32 issue peak (SMs x 128
+    lanes x max SM clock); the unit of work is one iteration (its forward and
+    adjoint launches).  Running sum with rows resident (Sec. 3, linear motion
+    blur): the fused per-iteration pass would move 12 B/px-it (f and u in, u'
+    out), counted as effective bytes against the measured copy bandwidth;
+    the unit of work is the one launch of the solve.  traffic: DRAM bytes per
+    unit from the ncu capture of these sources (profiles/), else None."""
+    px = SIZE * SIZE
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    if spec.kind == "disc":
+        r = spec.radius
+        per_unit = px * (4 * (2 * r + 1) + 4)
+        unit_ms = ms_solve / ITERS
+        peak = sms * 128 * sm_mhz * 1e6 / 1e12
+        achieved = per_unit / (unit_ms * 1e-3) / 1e12
+        persistent = launches == 1
+        if persistent:
+            kern = f"k_disc_persist<float, DiscOp<{r}>> (all {ITERS} iterations in one launch)"
+            traffic = traffic_of(cap, lambda k: re.match(rf"k_disc_persist<float, DiscOp<{r}[,>]", k) is not None)
+            traffic = traffic / ITERS if traffic is not None else None
+        else:
+            kern = f"k_disc_half<float, 0, DiscOp<{r}>, FWD> + <.., ADJ> (both launches of one iteration)"
+            traffic = traffic_of(cap, lambda k: re.match(rf"k_disc_half<float, 0, DiscOp<{r}[,>]", k) is not None)
+        return {"solve": spec.name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kern,
+                "unit_of_work": "one RL iteration on the 2048^2 image",
+                "algorithmic_per_unit": per_unit, "algorithmic_unit": "FP32 additions",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (additions)",
+                "hbm_equiv_gbs": 12 * px / (unit_ms * 1e-3) / 1e9,
+                "hbm_equiv_frac": 12 * px / (unit_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+    per_unit = 12 * px * ITERS
+    achieved = per_unit / (ms_solve * 1e-3) / 1e9
+    traffic = traffic_of(cap, lambda k: k.startswith("k_motion_x_tb<float, 0,"))
+    return {"solve": spec.name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "kernel": f"k_motion_x_tb<float> (rows resident for all {ITERS} iterations; "
+                      + ("along x)" if spec.axis == 0 else "on the transposed image)"),
+            "unit_of_work": f"one launch = the {ITERS}-iteration solve",
+            "algorithmic_per_unit": per_unit, "algorithmic_unit": "bytes of the fused per-iteration pass "
+                                                                 "(12 B/px-it), effective",
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"}
+
+
+def config1_run(local) -> dict:
+    """The 256^2 workload: motion-x 15, Gaussian noise sigma 2, 50 iterations,
+    FP32; rate and the error against the FP64 oracle on the same input."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1304_7211_gb300 import rl, synth
+    c = synth.config1()
+    f32 = c.f.astype(np.float32)
+    H, W = f32.shape
+    f = torch.from_numpy(f32).cuda(local)
+    u = torch.empty_like(f)
+    with rl.Deconvolver(c.spec, device=local) as d:
+        rl.rl_iterate(d.ctx, f, None, u, W, H, W, c.iterations)
+        ms = sorted(rl.rl_iterate(d.ctx, f, None, u, W, H, W, c.iterations, stats=True).device_ms
+                    for _ in range(7))
+    t = c.spec.dense()
+    ref = oracle.rl(f32.astype(np.float64), oracle.psf_dense(t, t.shape[1] // 2, t.shape[0] // 2),
+                    c.iterations).u
+    med = ms[len(ms) // 2]
+    return {"workload": f"{W}x{H} fp32, motion-x 15, Gaussian noise sigma 2, {c.iterations} it",
+            "value": W * H * c.iterations / med / 1e3, "unit": UNIT, "ms_per_solve": med,
+            "rel_linf_vs_oracle": oracle.rel_linf(u.cpu().numpy(), ref),
+            "timing": "CUDA events around rl_iterate (stats), median of 7; latency-bound at this size"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,7 +609,15 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--workload", default="plain", choices=["plain", "thinned"],
                     help="'thinned' prints the thinned-workload table instead of the bench line")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 4096^2 thinned sub-measurement")
+    ap.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "COMMAND"), default=None,
+                    help="write profiles/traffic_plain_2048.json from an ncu CSV (launch list with "
+                         "dram__bytes_{read,write}.sum) of COMMAND, tagged with this build's source hash")
     args = ap.parse_args()
+    if args.ingest_ncu:
+        out = ingest_ncu(args.ingest_ncu[0], TRAFFIC_FILE, WORKLOAD, args.ingest_ncu[1])
+        print(json.dumps(out, indent=1))
+        return 0
     ws, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
@@ -521,43 +717,26 @@ def main():
     e2e = e2e_rate / 1e6
     plane = SIZE * SIZE * 4
 
-    # dominant kernel: per-solve times, roofline of the slowest
-    per = {solves[i][0].name: solve_ms(i) for i in range(3)}
-    pk, pk_kind = peaks()
-    dom = max(per, key=per.get)
-    launch_ms = per[dom] / ITERS
-    px = SIZE * SIZE
-    if dom.startswith("disc"):
-        # span path: 2 (2r+1) additions per pixel per convolution (Sec. 3,
-        # generic box filter), two convolutions, plus ratio, update, scaling
-        r = 8
-        flops = px * (4 * (2 * r + 1) + 4)
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s, TFLOP/s (adds)
-        achieved = flops / (launch_ms * 1e-3) / 1e12
-        # DRAM bytes of one iteration (both launches): the ncu capture
-        # summarised in profiles/k_disc_half_disc8_2048.md predates moving the
-        # tile body into a device function shared with the batched kernel, so
-        # it is reported beside the line, not as this kernel's traffic
-        last_capture = 33.596928e6 + 0.003328e6 + 33.604352e6
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "traffic_last_capture": last_capture,
-                "kernel": f"k_disc_half<float,0,DiscOp<8>,FWD>+<..,ADJ> ({dom}, both launches of one iteration)",
-                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (adds)"}
-    else:
-        bytes_ = px * 12
-        achieved = bytes_ / (launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_source": pk_kind}
-    roof["per_solve_ms"] = per
-
     # kernel launches inside the timed region, as counted by the library
     launches_per_step = 0
+    launches = {}
     for spec, d, f, u, _, _ in solves:
         st = rl.rl_iterate(d.ctx, f, None, u, SIZE, SIZE, SIZE, ITERS, stats=True)
         launches_per_step += st.launches
+        launches[spec.name] = st.launches
+
+    # roofline of every solve's kernel; the top-level one is the slowest solve's
+    per = {solves[i][0].name: solve_ms(i) for i in range(3)}
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cap = measured_traffic()
+    rooflines = [solve_roofline(solves[i][0], per[solves[i][0].name], launches[solves[i][0].name], pk,
+                                pk_kind, sms, cap) for i in range(3)]
+    dom = max(range(3), key=lambda i: per[solves[i][0].name])
+    roof = dict(rooflines[dom])
+    roof["per_solve"] = rooflines
+    roof["traffic_capture"] = (os.path.relpath(TRAFFIC_FILE, ROOT) if cap is not None else
+                               "none for this build's sources (profiles/ capture predates a kernel change)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -569,9 +748,12 @@ def main():
                     "d2h_bytes_per_step": 3 * plane},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "clocks": clk}
+    line["config1"] = config1_run(local)
     if not args.no_batch:
         line["batch"] = batch_run(local)
         line["batch_tiles"] = tiles_run(local)
+    if not args.no_config3 and ws == 1:
+        line["config3"] = thinned_run(local)
     if not args.no_serve:
         line["serve"] = serve_run(local, n=args.serve_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
