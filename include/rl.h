@@ -243,11 +243,14 @@ const char *rl_last_error(const rl_ctx *ctx);
 /*
  * Batched execution of many independent deconvolutions (the batched and
  * served workloads): a batch owns `slots` CUDA streams, each with its own
- * context and scratch.  rl_batch_submit places a job on the slot with the
- * least queued work (pixel-iterations) and returns at once; jobs on
+ * context and scratch.  rl_batch_submit copies the job into a host queue and
+ * returns at once; queued jobs are issued in submission order, each to the
+ * slot with the least queued work (pixel-iterations), while that slot has
+ * fewer than two jobs on the GPU.  Every batch call issues what fits.  Jobs on
  * different slots overlap on the GPU, jobs on one slot run in order.  Each
  * job's result depends only on its own inputs (no cross-job state), so a job
- * gives the same image alone and in any mix.
+ * gives the same image alone and in any mix, and a job that fails (bad PSF,
+ * out of memory) fails alone: the others run on.
  *
  *   f, u0 (NULL = f), u_out: device pointers, caller-owned, valid until the
  *       job is done; u_out may alias u0 but not f.
@@ -256,7 +259,10 @@ const char *rl_last_error(const rl_ctx *ctx);
  *       after it runs.  Both use row pitch W elements.
  *   psf: copied at submit.  thin: nullable, copied at submit (a schedule
  *       pointer inside must stay valid until the job is done).
- * Errors: as rl_set_psf / rl_iterate; RL_ERR_INVALID_ARG for a bad ticket.
+ * Errors: as rl_set_psf / rl_iterate, returned by rl_batch_submit when the
+ * job is issued inside that call, else by rl_batch_query / rl_batch_wait of
+ * its ticket; RL_ERR_INVALID_ARG for a bad ticket.  No C++ exception crosses
+ * the ABI: host allocation failures come back as RL_ERR_OOM.
  */
 typedef struct {
     const void *f;
@@ -278,13 +284,22 @@ typedef struct rl_batch rl_batch;
 rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out);
 /* Queue a job; *ticket identifies it for rl_batch_query / rl_batch_wait. */
 rl_status rl_batch_submit(rl_batch *b, const rl_job *job, long long *ticket);
-/* *done = 1 when the job's work (and its download) has finished. */
+/* *done = 1 when the job's work (and its download) has finished, or when it
+ * was cancelled or failed (then its status is returned). */
 rl_status rl_batch_query(rl_batch *b, long long ticket, int *done);
 /* Block until the job has finished. */
 rl_status rl_batch_wait(rl_batch *b, long long ticket);
 /* Block until every submitted job has finished. */
 rl_status rl_batch_sync(rl_batch *b);
-/* Wait for all jobs, then release streams, contexts and scratch. NULL-safe. */
+/* Cancel a job.  Not yet issued: it is dropped and never runs (*was_running
+ * = 0).  Already on the GPU: it cannot be stopped; it runs to the end, may
+ * still write u_out / u_host, and its result is to be discarded (*was_running
+ * = 1).  Either way its ticket then reports done with RL_OK.  RL_ERR_STATE if
+ * the job has already finished, failed or been cancelled; RL_ERR_INVALID_ARG
+ * for an unknown ticket.  was_running may be NULL. */
+rl_status rl_batch_cancel(rl_batch *b, long long ticket, int *was_running);
+/* Drop the jobs not yet issued, wait for the issued ones, then release
+ * streams, contexts and scratch.  NULL-safe. */
 rl_status rl_batch_destroy(rl_batch *b);
 /* Message of the last failure on b. */
 const char *rl_batch_last_error(const rl_batch *b);
@@ -328,6 +343,15 @@ const char *rl_version(void);
  * small buffers; no context is needed.  No counterpart in the paper.
  */
 rl_status rl_selftest_wait_timeout(int device, int wait_ms);
+
+/*
+ * Fault injection for tests (host side, no GPU fault): with nth > 0 the
+ * nth scratch allocation that rl_iterate, rl_iterate_tiles or a batch job
+ * makes from now on, in any context of the process, fails as if the device
+ * were out of memory -- the call returns RL_ERR_OOM with a message and the
+ * context stays usable.  0 disables.  No counterpart in the paper.
+ */
+void rl_test_fail_allocation(int nth);
 
 /*
  * Allocation-free variant of the running-sum path.  The paper has no

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -133,6 +134,27 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Fault injection for tests: when set to n > 0, the n-th scratch allocation
+// from then on fails as if the device were out of memory.
+std::atomic<int> g_fail_alloc{0};
+
+// Every scratch allocation of rl_iterate: stream-ordered on the context
+// stream (no device-wide synchronisation, unlike cudaMalloc / cudaFree).
+rl_status salloc(rl_ctx *ctx, void **p, size_t bytes, const char *what) {
+    int n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) return fail(ctx, RL_ERR_OOM, std::string(what) + ": injected allocation failure");
+    CK(cudaMallocAsync(p, bytes, ctx->stream), what);
+    return RL_OK;
+}
+
+#define SALLOC(pp, bytes, what)                                   \
+    do {                                                          \
+        rl_status st_ = salloc(ctx, (void **)(pp), (bytes), what); \
+        if (st_ != RL_OK) return st_;                             \
+    } while (0)
+
 // Scratch growth in stream order on the context stream: the old buffer is
 // released after the work already queued there, and no other stream (of a
 // batch, say) is waited on, as cudaFree would.
@@ -141,13 +163,35 @@ rl_status grow(rl_ctx *ctx, void **p, size_t *have, size_t need, const char *wha
     if (*p) cudaFreeAsync(*p, ctx->stream);
     *p = nullptr;
     *have = 0;
-    CK(cudaMallocAsync(p, need, ctx->stream), what);
+    SALLOC(p, need, what);
     *have = need;
     return RL_OK;
 }
 
 void sfree(rl_ctx *ctx, void *p) {
     if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+// No C++ exception crosses the C ABI: a host allocation failure inside an
+// entry point (std::vector / std::string growth) becomes RL_ERR_OOM,
+// anything else RL_ERR_STATE, with the context's message set if it can be.
+template <typename F>
+rl_status abi_guard(rl_ctx *ctx, F &&fn) noexcept {
+    try {
+        return fn();
+    } catch (const std::bad_alloc &) {
+        try {
+            if (ctx) ctx->err = "out of host memory";
+        } catch (...) {
+        }
+        return RL_ERR_OOM;
+    } catch (...) {
+        try {
+            if (ctx) ctx->err = "internal error";
+        } catch (...) {
+        }
+        return RL_ERR_STATE;
+    }
 }
 
 }  // namespace
@@ -160,7 +204,7 @@ const char *rl_last_error(const rl_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_create_error.c_str();
 }
 
-rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
+static rl_status create_impl(const rl_config *cfg, rl_ctx **out) {
     g_create_error.clear();
     if (!out) {
         g_create_error = "rl_create: out is NULL";
@@ -232,7 +276,7 @@ rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
     return RL_OK;
 }
 
-rl_status rl_destroy(rl_ctx *ctx) {
+static rl_status destroy_impl(rl_ctx *ctx) {
     if (!ctx) return RL_OK;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -281,7 +325,7 @@ rl_status rl_destroy(rl_ctx *ctx) {
     return RL_OK;
 }
 
-rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
+static rl_status set_psf_impl(rl_ctx *ctx, const rl_psf_desc *d) {
     if (!ctx) return RL_ERR_INVALID_ARG;
     if (!d) return fail(ctx, RL_ERR_INVALID_ARG, "rl_set_psf: descriptor is NULL");
     std::vector<double> t;
@@ -640,8 +684,8 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
             sfree(ctx, ctx->tbuf[1]);
             ctx->tbuf[0] = ctx->tbuf[1] = nullptr;
             ctx->tbuf_bytes = 0;
-            CK(cudaMallocAsync(&ctx->tbuf[0], tbytes, ctx->stream), "rl_iterate: transposed f");
-            CK(cudaMallocAsync(&ctx->tbuf[1], tbytes, ctx->stream), "rl_iterate: transposed u");
+            SALLOC(&ctx->tbuf[0], tbytes, "rl_iterate: transposed f");
+            SALLOC(&ctx->tbuf[1], tbytes, "rl_iterate: transposed u");
             ctx->tbuf_bytes = tbytes;
         }
         CK(rl::launch_transpose(f, pitch, 0, ctx->tbuf[0], tp, 0, W, H, 1, (int)es, ctx->stream),
@@ -716,8 +760,8 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         sfree(ctx, ctx->ubuf[1]);
         ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
         ctx->ubuf_bytes = 0;
-        CK(cudaMallocAsync(&ctx->ubuf[0], plane * es, ctx->stream), "rl_iterate: scratch u");
-        CK(cudaMallocAsync(&ctx->ubuf[1], plane * es, ctx->stream), "rl_iterate: scratch u");
+        SALLOC(&ctx->ubuf[0], plane * es, "rl_iterate: scratch u");
+        SALLOC(&ctx->ubuf[1], plane * es, "rl_iterate: scratch u");
         ctx->ubuf_bytes = plane * es;
     }
     IterArgs a;
@@ -774,7 +818,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
                 sfree(ctx, ctx->tflags);
                 ctx->tflags = nullptr;
                 ctx->tflags_n = 0;
-                CK(cudaMallocAsync((void **)&ctx->tflags, n * sizeof(int), ctx->stream), "rl_iterate: tile flags");
+                SALLOC((void **)&ctx->tflags, n * sizeof(int), "rl_iterate: tile flags");
                 ctx->tflags_n = n;
             }
             a.tile_flags = ctx->tflags;
@@ -913,9 +957,9 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             ctx->rstale = nullptr;
             ctx->thin_px = 0;
             ctx->last_mask = nullptr;
-            CK(cudaMallocAsync((void **)&ctx->mask[0], plane, ctx->stream), "rl_iterate: mask");
-            CK(cudaMallocAsync((void **)&ctx->mask[1], plane, ctx->stream), "rl_iterate: mask");
-            CK(cudaMallocAsync((void **)&ctx->rstale, plane * sizeof(float), ctx->stream), "rl_iterate: stale ratio");
+            SALLOC((void **)&ctx->mask[0], plane, "rl_iterate: mask");
+            SALLOC((void **)&ctx->mask[1], plane, "rl_iterate: mask");
+            SALLOC((void **)&ctx->rstale, plane * sizeof(float), "rl_iterate: stale ratio");
             ctx->thin_px = plane;
         }
         CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream),
@@ -945,8 +989,8 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         sfree(ctx, ctx->ubuf[1]);
         ctx->ubuf[0] = ctx->ubuf[1] = nullptr;
         ctx->ubuf_bytes = 0;
-        CK(cudaMallocAsync(&ctx->ubuf[0], plane * es, ctx->stream), "rl_iterate: scratch u");
-        CK(cudaMallocAsync(&ctx->ubuf[1], plane * es, ctx->stream), "rl_iterate: scratch u");
+        SALLOC(&ctx->ubuf[0], plane * es, "rl_iterate: scratch u");
+        SALLOC(&ctx->ubuf[1], plane * es, "rl_iterate: scratch u");
         ctx->ubuf_bytes = plane * es;
     }
     // the register-blocked two-half kernels: the disc; a uniform centred
@@ -967,7 +1011,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
             sfree(ctx, ctx->qplane);
             ctx->qplane = nullptr;
             ctx->q_px = 0;
-            CK(cudaMallocAsync((void **)&ctx->qplane, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
+            SALLOC((void **)&ctx->qplane, plane * sizeof(float), "rl_iterate: ratio plane");
             ctx->q_px = plane;
         }
         if (thin) CK(cudaMemsetAsync(ctx->qplane, 0, plane * sizeof(float), ctx->stream), "rl_iterate: ratio plane");
@@ -1083,9 +1127,8 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
 
 }  // namespace
 
-extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W,
-                                int H, long long pitch, int iterations, const rl_thinning *thin,
-                                rl_stats *stats) {
+static rl_status iterate_impl(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W, int H,
+                              long long pitch, int iterations, const rl_thinning *thin, rl_stats *stats) {
     if (!ctx) return RL_ERR_INVALID_ARG;
     if (!f || !u_out) return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate: f and u_out must not be NULL");
     if (W < 1 || H < 1 || pitch < W || iterations < 0)
@@ -1208,7 +1251,7 @@ extern "C" rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void
     return RL_OK;
 }
 
-extern "C" rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n) {
+static rl_status iterate_tiles_impl(rl_ctx *ctx, const rl_job *jobs, int n) {
     if (!ctx) return RL_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && !jobs)) return fail(ctx, RL_ERR_INVALID_ARG, "rl_iterate_tiles: need n >= 0 and jobs");
     if (!ctx->has_psf) return fail(ctx, RL_ERR_STATE, "rl_iterate_tiles: no PSF set");
@@ -1294,8 +1337,7 @@ extern "C" rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n) {
     const size_t jobs_bytes = (n * sizeof(rl::TileJob) + 255) / 256 * 256;
     const size_t items_bytes = std::max<size_t>(items.size(), 1) * sizeof(int2);
     char *scratch = nullptr;
-    CK(cudaMallocAsync((void **)&scratch, plane_bytes + jobs_bytes + items_bytes, ctx->stream),
-       "rl_iterate_tiles: scratch");
+    SALLOC((void **)&scratch, plane_bytes + jobs_bytes + items_bytes, "rl_iterate_tiles: scratch");
     struct Free {
         char *p;
         cudaStream_t s;
@@ -1357,7 +1399,7 @@ extern "C" rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n) {
     return RL_OK;
 }
 
-extern "C" rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch) {
+static rl_status get_mask_impl(rl_ctx *ctx, void *dst, long long dst_pitch) {
     if (!ctx) return RL_ERR_INVALID_ARG;
     if (!dst) return fail(ctx, RL_ERR_INVALID_ARG, "rl_get_mask: dst is NULL");
     if (!ctx->last_mask) return fail(ctx, RL_ERR_STATE, "rl_get_mask: no thinned iteration has run");
@@ -1378,7 +1420,7 @@ extern "C" rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch) {
 // iteration, so every adjoint item waits for neighbours that never finish.
 // Each wait gives up after wait_ms, the kernel records status 1 and every CTA
 // returns; the context stays usable.
-extern "C" rl_status rl_selftest_wait_timeout(int device, int wait_ms) {
+static rl_status selftest_wait_timeout_impl(int device, int wait_ms) {
     if (wait_ms < 1 || wait_ms > 10000) return RL_ERR_INVALID_ARG;
     int prev = 0;
     if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
@@ -1433,3 +1475,37 @@ extern "C" rl_status rl_selftest_wait_timeout(int device, int wait_ms) {
     cudaSetDevice(prev);
     return st;
 }
+
+// ---- C ABI entry points ------------------------------------------------------
+extern "C" {
+
+rl_status rl_create(const rl_config *cfg, rl_ctx **out) {
+    return abi_guard(nullptr, [&] { return create_impl(cfg, out); });
+}
+
+rl_status rl_destroy(rl_ctx *ctx) { return abi_guard(nullptr, [&] { return destroy_impl(ctx); }); }
+
+rl_status rl_set_psf(rl_ctx *ctx, const rl_psf_desc *d) {
+    return abi_guard(ctx, [&] { return set_psf_impl(ctx, d); });
+}
+
+rl_status rl_iterate(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W, int H, long long pitch,
+                     int iterations, const rl_thinning *thin, rl_stats *stats) {
+    return abi_guard(ctx, [&] { return iterate_impl(ctx, f, u0, u_out, W, H, pitch, iterations, thin, stats); });
+}
+
+rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n) {
+    return abi_guard(ctx, [&] { return iterate_tiles_impl(ctx, jobs, n); });
+}
+
+rl_status rl_get_mask(rl_ctx *ctx, void *dst, long long dst_pitch) {
+    return abi_guard(ctx, [&] { return get_mask_impl(ctx, dst, dst_pitch); });
+}
+
+rl_status rl_selftest_wait_timeout(int device, int wait_ms) {
+    return abi_guard(nullptr, [&] { return selftest_wait_timeout_impl(device, wait_ms); });
+}
+
+void rl_test_fail_allocation(int nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }
+
+}  // extern "C"

@@ -1,11 +1,14 @@
 // rl_batch.cu -- batched execution of independent deconvolutions on several
 // CUDA streams (declared in include/rl.h).  Each slot is a non-blocking
-// stream with its own context (PSF, scratch); the scheduler places a job on
-// the slot with the least queued pixel-iterations, so small images from
-// different jobs share the GPU while each job's own iterations stay in order.
+// stream with its own context (PSF, scratch).  Submitted jobs wait in a host
+// queue; a job is issued to the slot with the least queued pixel-iterations
+// once that slot has fewer than kDepth jobs in flight, so small images from
+// different jobs share the GPU while each job's own iterations stay in order,
+// and a job that has not been issued yet can still be cancelled.
 #include <cuda_runtime.h>
 
 #include <deque>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -14,17 +17,35 @@
 
 namespace {
 
+constexpr int kDepth = 2;  // jobs in flight per slot
+
+struct Job {
+    long long ticket;
+    rl_job job;
+    std::vector<float> taps;  // copy of job.psf.taps
+    rl_thinning thin;         // copy of *job.thin
+    bool has_thin;
+    long long work;           // pixel-iterations
+};
+
 struct Pending {
     long long ticket;
     cudaEvent_t done;
-    long long work;  // pixel-iterations
+    long long work;
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
     rl_ctx *ctx = nullptr;
-    std::deque<Pending> queue;  // submitted, possibly unfinished
+    std::deque<Pending> queue;  // issued, possibly unfinished
     long long queued_work = 0;
+};
+
+// Jobs that did not finish normally: failed when issued, or cancelled.
+struct Outcome {
+    rl_status status;
+    std::string message;
+    bool cancelled;
 };
 
 }  // namespace
@@ -33,7 +54,9 @@ struct rl_batch {
     int device = 0;
     int storage = RL_STORAGE_F32;
     std::vector<Slot> slots;
+    std::deque<Job> waiting;  // submitted, not issued
     std::vector<cudaEvent_t> free_events;
+    std::map<long long, Outcome> outcomes;
     long long next_ticket = 1;
     std::string err;
 };
@@ -57,11 +80,107 @@ void reap(rl_batch *b) {
     }
 }
 
-Pending *find(rl_batch *b, long long ticket) {
+Pending *find_issued(rl_batch *b, long long ticket) {
     for (auto &s : b->slots)
         for (auto &p : s.queue)
             if (p.ticket == ticket) return &p;
     return nullptr;
+}
+
+bool is_waiting(const rl_batch *b, long long ticket) {
+    for (const auto &j : b->waiting)
+        if (j.ticket == ticket) return true;
+    return false;
+}
+
+// Enqueue one job on slot s: PSF, optional upload, the solve, optional
+// download, completion event.  On failure nothing of the job stays queued
+// beyond what the stream already holds; the status says why.
+rl_status issue(rl_batch *b, Slot &s, Job &j, std::string *msg) {
+    rl_job &job = j.job;
+    job.psf.taps = j.taps.empty() ? nullptr : j.taps.data();
+    rl_status st = rl_set_psf(s.ctx, &job.psf);
+    if (st != RL_OK) {
+        *msg = rl_last_error(s.ctx);
+        return st;
+    }
+    const size_t esz = b->storage == RL_STORAGE_F32 ? 4 : 2;
+    if (job.f_host) {
+        cudaError_t e = cudaMemcpy2DAsync((void *)job.f, job.pitch * esz, job.f_host, job.W * esz, job.W * esz,
+                                          job.H, cudaMemcpyHostToDevice, s.stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *msg = std::string("rl_batch: upload: ") + cudaGetErrorString(e);
+            return RL_ERR_CUDA;
+        }
+    }
+    st = rl_iterate(s.ctx, job.f, job.u0, job.u_out, job.W, job.H, job.pitch, job.iterations,
+                    j.has_thin ? &j.thin : nullptr, nullptr);
+    if (st != RL_OK) {
+        *msg = rl_last_error(s.ctx);
+        return st;
+    }
+    if (job.u_host) {
+        cudaError_t e = cudaMemcpy2DAsync(job.u_host, job.W * esz, job.u_out, job.pitch * esz, job.W * esz,
+                                          job.H, cudaMemcpyDeviceToHost, s.stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *msg = std::string("rl_batch: download: ") + cudaGetErrorString(e);
+            return RL_ERR_CUDA;
+        }
+    }
+    cudaEvent_t ev;
+    if (!b->free_events.empty()) {
+        ev = b->free_events.back();
+        b->free_events.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *msg = "rl_batch: event";
+        return RL_ERR_CUDA;
+    }
+    cudaEventRecord(ev, s.stream);
+    s.queue.push_back({j.ticket, ev, j.work});
+    s.queued_work += j.work;
+    return RL_OK;
+}
+
+// Issue waiting jobs in submission order while some slot has room.  A job
+// whose issue fails is recorded as failed; the others go on.  Returns the
+// status of the job `watch` if it was issued (or failed) here, else RL_OK.
+rl_status pump(rl_batch *b, long long watch = 0, std::string *watch_msg = nullptr) {
+    reap(b);
+    rl_status watched = RL_OK;
+    while (!b->waiting.empty()) {
+        Slot *best = nullptr;
+        for (auto &s : b->slots)
+            if ((int)s.queue.size() < kDepth && (!best || s.queued_work < best->queued_work)) best = &s;
+        if (!best) break;
+        Job j = std::move(b->waiting.front());
+        b->waiting.pop_front();
+        std::string msg;
+        const rl_status st = issue(b, *best, j, &msg);
+        if (st != RL_OK) {
+            b->outcomes[j.ticket] = {st, msg, false};
+            if (j.ticket == watch) {
+                watched = st;
+                if (watch_msg) *watch_msg = msg;
+            }
+        }
+    }
+    return watched;
+}
+
+// Block until some issued job finishes (the slot with the most queued work
+// first), so that a waiting job can be issued.
+rl_status wait_any(rl_batch *b) {
+    Slot *busiest = nullptr;
+    for (auto &s : b->slots)
+        if (!s.queue.empty() && (!busiest || s.queued_work > busiest->queued_work)) busiest = &s;
+    if (!busiest) return RL_OK;
+    const cudaError_t e = cudaEventSynchronize(busiest->queue.front().done);
+    if (e != cudaSuccess) return bfail(b, RL_ERR_CUDA, std::string("rl_batch: ") + cudaGetErrorString(e));
+    reap(b);
+    return RL_OK;
 }
 
 struct DeviceGuard {
@@ -73,144 +192,211 @@ struct DeviceGuard {
     ~DeviceGuard() { cudaSetDevice(prev); }
 };
 
+// No C++ exception crosses the C ABI: an allocation failure inside becomes
+// RL_ERR_OOM, anything else RL_ERR_STATE.
+template <typename F>
+rl_status guarded(rl_batch *b, F &&fn) {
+    try {
+        return fn();
+    } catch (const std::bad_alloc &) {
+        if (b) b->err = "out of host memory";
+        return RL_ERR_OOM;
+    } catch (...) {
+        if (b) b->err = "internal error";
+        return RL_ERR_STATE;
+    }
+}
+
 }  // namespace
 
 extern "C" {
 
 rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out) {
-    if (!out || slots < 1 || slots > 256) return RL_ERR_INVALID_ARG;
-    *out = nullptr;
-    rl_config c = {0, nullptr, RL_STORAGE_F32, RL_BOUNDARY_MIRROR, RL_PATH_AUTO, 0};
-    if (cfg) c = *cfg;
-    rl_batch *b = new (std::nothrow) rl_batch;
-    if (!b) return RL_ERR_OOM;
-    b->device = c.device;
-    b->storage = c.storage;
-    DeviceGuard g(c.device);
-    b->slots.resize(slots);
-    for (auto &s : b->slots) {
-        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
-            (void)cudaGetLastError();
-            rl_batch_destroy(b);
-            return RL_ERR_CUDA;
+    return guarded(nullptr, [&]() -> rl_status {
+        if (!out || slots < 1 || slots > 256) return RL_ERR_INVALID_ARG;
+        *out = nullptr;
+        rl_config c = {0, nullptr, RL_STORAGE_F32, RL_BOUNDARY_MIRROR, RL_PATH_AUTO, 0};
+        if (cfg) c = *cfg;
+        rl_batch *b = new (std::nothrow) rl_batch;
+        if (!b) return RL_ERR_OOM;
+        b->device = c.device;
+        b->storage = c.storage;
+        DeviceGuard g(c.device);
+        b->slots.resize(slots);
+        for (auto &s : b->slots) {
+            if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
+                (void)cudaGetLastError();
+                rl_batch_destroy(b);
+                return RL_ERR_CUDA;
+            }
+            rl_config sc = c;
+            sc.stream = s.stream;
+            rl_status st = rl_create(&sc, &s.ctx);
+            if (st != RL_OK) {
+                rl_batch_destroy(b);
+                return st;
+            }
         }
-        rl_config sc = c;
-        sc.stream = s.stream;
-        rl_status st = rl_create(&sc, &s.ctx);
-        if (st != RL_OK) {
-            rl_batch_destroy(b);
-            return st;
-        }
-    }
-    *out = b;
-    return RL_OK;
+        *out = b;
+        return RL_OK;
+    });
 }
 
 rl_status rl_batch_submit(rl_batch *b, const rl_job *job, long long *ticket) {
     if (!b) return RL_ERR_INVALID_ARG;
-    if (!job || !ticket) return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_submit: job and ticket are required");
-    if (!job->f || !job->u_out || job->W < 1 || job->H < 1 || job->pitch < job->W || job->iterations < 0)
-        return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_submit: bad job geometry or buffers");
-    DeviceGuard g(b->device);
-    reap(b);
-    Slot *best = &b->slots[0];
-    for (auto &s : b->slots)
-        if (s.queued_work < best->queued_work) best = &s;
-    Slot &s = *best;
-    rl_status st = rl_set_psf(s.ctx, &job->psf);
-    if (st != RL_OK) return bfail(b, st, rl_last_error(s.ctx));
-    const size_t esz = b->storage == RL_STORAGE_F32 ? 4 : 2;
-    if (job->f_host) {
-        cudaError_t e = cudaMemcpy2DAsync((void *)job->f, job->pitch * esz, job->f_host, job->W * esz,
-                                          job->W * esz, job->H, cudaMemcpyHostToDevice, s.stream);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            return bfail(b, RL_ERR_CUDA, std::string("rl_batch_submit: upload: ") + cudaGetErrorString(e));
+    return guarded(b, [&]() -> rl_status {
+        if (!job || !ticket) return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_submit: job and ticket are required");
+        if (!job->f || !job->u_out || job->W < 1 || job->H < 1 || job->pitch < job->W || job->iterations < 0)
+            return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_submit: bad job geometry or buffers");
+        if (job->psf.kind == RL_PSF_DENSE && (!job->psf.taps || job->psf.kw < 1 || job->psf.kh < 1))
+            return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_submit: dense PSF without taps");
+        DeviceGuard g(b->device);
+        Job j;
+        j.ticket = b->next_ticket++;
+        j.job = *job;
+        if (job->psf.kind == RL_PSF_DENSE)
+            j.taps.assign(job->psf.taps, job->psf.taps + (size_t)job->psf.kw * job->psf.kh);
+        j.has_thin = job->thin != nullptr;
+        if (j.has_thin) j.thin = *job->thin;
+        j.job.thin = nullptr;
+        j.work = (long long)job->W * job->H * (job->iterations > 0 ? job->iterations : 1);
+        const long long t = j.ticket;
+        b->waiting.push_back(std::move(j));
+        std::string msg;
+        const rl_status st = pump(b, t, &msg);
+        if (st != RL_OK) {
+            // failed as it was issued, inside this call: report it here
+            b->outcomes.erase(t);
+            return bfail(b, st, msg);
         }
-    }
-    st = rl_iterate(s.ctx, job->f, job->u0, job->u_out, job->W, job->H, job->pitch, job->iterations,
-                    job->thin, nullptr);
-    if (st != RL_OK) return bfail(b, st, rl_last_error(s.ctx));
-    if (job->u_host) {
-        cudaError_t e = cudaMemcpy2DAsync(job->u_host, job->W * esz, job->u_out, job->pitch * esz,
-                                          job->W * esz, job->H, cudaMemcpyDeviceToHost, s.stream);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            return bfail(b, RL_ERR_CUDA, std::string("rl_batch_submit: download: ") + cudaGetErrorString(e));
-        }
-    }
-    cudaEvent_t ev;
-    if (!b->free_events.empty()) {
-        ev = b->free_events.back();
-        b->free_events.pop_back();
-    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return bfail(b, RL_ERR_CUDA, "rl_batch_submit: event");
-    }
-    cudaEventRecord(ev, s.stream);
-    const long long work = (long long)job->W * job->H * (job->iterations > 0 ? job->iterations : 1);
-    s.queue.push_back({b->next_ticket, ev, work});
-    s.queued_work += work;
-    *ticket = b->next_ticket++;
-    return RL_OK;
+        *ticket = t;
+        return RL_OK;
+    });
 }
 
 rl_status rl_batch_query(rl_batch *b, long long ticket, int *done) {
     if (!b || !done) return RL_ERR_INVALID_ARG;
-    DeviceGuard g(b->device);
-    Pending *p = find(b, ticket);
-    if (!p) {
-        // not queued any more: finished and reaped, or never issued
-        *done = ticket > 0 && ticket < b->next_ticket;
-        return *done ? RL_OK : bfail(b, RL_ERR_INVALID_ARG, "rl_batch_query: unknown ticket");
-    }
-    const cudaError_t e = cudaEventQuery(p->done);
-    if (e != cudaSuccess && e != cudaErrorNotReady) {
+    return guarded(b, [&]() -> rl_status {
+        DeviceGuard g(b->device);
+        pump(b);
+        auto o = b->outcomes.find(ticket);
+        if (o != b->outcomes.end()) {
+            *done = 1;
+            return o->second.cancelled ? RL_OK : bfail(b, o->second.status, o->second.message);
+        }
+        if (is_waiting(b, ticket)) {
+            *done = 0;
+            return RL_OK;
+        }
+        Pending *p = find_issued(b, ticket);
+        if (!p) {
+            // not queued any more: finished and reaped, or never issued
+            *done = ticket > 0 && ticket < b->next_ticket;
+            return *done ? RL_OK : bfail(b, RL_ERR_INVALID_ARG, "rl_batch_query: unknown ticket");
+        }
+        const cudaError_t e = cudaEventQuery(p->done);
+        if (e != cudaSuccess && e != cudaErrorNotReady) {
+            (void)cudaGetLastError();
+            return bfail(b, RL_ERR_CUDA, std::string("rl_batch_query: ") + cudaGetErrorString(e));
+        }
         (void)cudaGetLastError();
-        return bfail(b, RL_ERR_CUDA, std::string("rl_batch_query: ") + cudaGetErrorString(e));
-    }
-    (void)cudaGetLastError();
-    *done = e == cudaSuccess;
-    return RL_OK;
+        *done = e == cudaSuccess;
+        return RL_OK;
+    });
 }
 
 rl_status rl_batch_wait(rl_batch *b, long long ticket) {
     if (!b) return RL_ERR_INVALID_ARG;
-    DeviceGuard g(b->device);
-    Pending *p = find(b, ticket);
-    if (!p) return ticket > 0 && ticket < b->next_ticket ? RL_OK
-                                                         : bfail(b, RL_ERR_INVALID_ARG, "rl_batch_wait: unknown ticket");
-    const cudaError_t e = cudaEventSynchronize(p->done);
-    if (e != cudaSuccess) return bfail(b, RL_ERR_CUDA, std::string("rl_batch_wait: ") + cudaGetErrorString(e));
-    reap(b);
-    return RL_OK;
+    return guarded(b, [&]() -> rl_status {
+        DeviceGuard g(b->device);
+        if (ticket <= 0 || ticket >= b->next_ticket)
+            return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_wait: unknown ticket");
+        for (;;) {
+            pump(b);
+            auto o = b->outcomes.find(ticket);
+            if (o != b->outcomes.end())
+                return o->second.cancelled ? RL_OK : bfail(b, o->second.status, o->second.message);
+            if (is_waiting(b, ticket)) {
+                rl_status st = wait_any(b);
+                if (st != RL_OK) return st;
+                continue;
+            }
+            Pending *p = find_issued(b, ticket);
+            if (!p) return RL_OK;  // finished and reaped
+            const cudaError_t e = cudaEventSynchronize(p->done);
+            if (e != cudaSuccess) return bfail(b, RL_ERR_CUDA, std::string("rl_batch_wait: ") + cudaGetErrorString(e));
+            reap(b);
+            return RL_OK;
+        }
+    });
 }
 
 rl_status rl_batch_sync(rl_batch *b) {
     if (!b) return RL_ERR_INVALID_ARG;
-    DeviceGuard g(b->device);
-    for (auto &s : b->slots) {
-        const cudaError_t e = cudaStreamSynchronize(s.stream);
-        if (e != cudaSuccess) return bfail(b, RL_ERR_CUDA, std::string("rl_batch_sync: ") + cudaGetErrorString(e));
-    }
-    reap(b);
-    return RL_OK;
+    return guarded(b, [&]() -> rl_status {
+        DeviceGuard g(b->device);
+        for (;;) {
+            pump(b);
+            if (b->waiting.empty()) break;
+            rl_status st = wait_any(b);
+            if (st != RL_OK) return st;
+        }
+        for (auto &s : b->slots) {
+            const cudaError_t e = cudaStreamSynchronize(s.stream);
+            if (e != cudaSuccess) return bfail(b, RL_ERR_CUDA, std::string("rl_batch_sync: ") + cudaGetErrorString(e));
+        }
+        reap(b);
+        return RL_OK;
+    });
+}
+
+rl_status rl_batch_cancel(rl_batch *b, long long ticket, int *was_running) {
+    if (!b) return RL_ERR_INVALID_ARG;
+    return guarded(b, [&]() -> rl_status {
+        DeviceGuard g(b->device);
+        reap(b);
+        if (was_running) *was_running = 0;
+        if (b->outcomes.count(ticket))
+            return bfail(b, RL_ERR_STATE, "rl_batch_cancel: the job already failed or was cancelled");
+        for (auto it = b->waiting.begin(); it != b->waiting.end(); ++it) {
+            if (it->ticket == ticket) {
+                b->waiting.erase(it);
+                b->outcomes[ticket] = {RL_OK, "cancelled before it started", true};
+                return RL_OK;
+            }
+        }
+        Pending *p = find_issued(b, ticket);
+        if (p && cudaEventQuery(p->done) == cudaErrorNotReady) {
+            (void)cudaGetLastError();
+            // on the GPU already: it runs to the end; its result is discarded
+            b->outcomes[ticket] = {RL_OK, "cancelled while running", true};
+            if (was_running) *was_running = 1;
+            return RL_OK;
+        }
+        (void)cudaGetLastError();
+        if (ticket > 0 && ticket < b->next_ticket)
+            return bfail(b, RL_ERR_STATE, "rl_batch_cancel: the job has already finished");
+        return bfail(b, RL_ERR_INVALID_ARG, "rl_batch_cancel: unknown ticket");
+    });
 }
 
 rl_status rl_batch_destroy(rl_batch *b) {
     if (!b) return RL_OK;
-    {
-        DeviceGuard g(b->device);
-        for (auto &s : b->slots) {
-            if (s.stream) cudaStreamSynchronize(s.stream);
-            rl_destroy(s.ctx);
-            for (auto &p : s.queue) cudaEventDestroy(p.done);
-            if (s.stream) cudaStreamDestroy(s.stream);
+    return guarded(nullptr, [&]() -> rl_status {
+        {
+            DeviceGuard g(b->device);
+            b->waiting.clear();  // never issued: dropped
+            for (auto &s : b->slots) {
+                if (s.stream) cudaStreamSynchronize(s.stream);
+                rl_destroy(s.ctx);
+                for (auto &p : s.queue) cudaEventDestroy(p.done);
+                if (s.stream) cudaStreamDestroy(s.stream);
+            }
+            for (auto ev : b->free_events) cudaEventDestroy(ev);
         }
-        for (auto ev : b->free_events) cudaEventDestroy(ev);
-    }
-    delete b;
-    return RL_OK;
+        delete b;
+        return RL_OK;
+    });
 }
 
 const char *rl_batch_last_error(const rl_batch *b) { return b ? b->err.c_str() : ""; }

@@ -50,9 +50,8 @@ bool on_device(const void *p, int dev) {
 
 }  // namespace
 
-extern "C" rl_status rl_motion_x_noalloc(const float *f, const float *u0, float *u_out, int W,
-                                         int H, long long pitch, int length, int boundary,
-                                         int iterations, void *stream, char *err, int err_len) {
+static rl_status noalloc_impl(const float *f, const float *u0, float *u_out, int W, int H, long long pitch,
+                              int length, int boundary, int iterations, void *stream, char *err, int err_len) {
     set_err(err, err_len, "");
     if (!f || !u_out || u_out == f || (u0 && u_out == u0)) {
         set_err(err, err_len, "rl_motion_x_noalloc: f and u_out are required; u_out must not alias f or u0");
@@ -150,4 +149,17 @@ extern "C" rl_status rl_motion_x_noalloc(const float *f, const float *u0, float 
         in_pitch = a.out_pitch;
     }
     return RL_OK;
+}
+
+// No C++ exception crosses the C ABI (the set-up lock is the only thing here
+// that could throw).
+extern "C" rl_status rl_motion_x_noalloc(const float *f, const float *u0, float *u_out, int W,
+                                         int H, long long pitch, int length, int boundary,
+                                         int iterations, void *stream, char *err, int err_len) {
+    try {
+        return noalloc_impl(f, u0, u_out, W, H, pitch, length, boundary, iterations, stream, err, err_len);
+    } catch (...) {
+        set_err(err, err_len, "rl_motion_x_noalloc: internal error");
+        return RL_ERR_STATE;
+    }
 }

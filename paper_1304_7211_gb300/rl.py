@@ -88,7 +88,8 @@ _lib = None
 EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error", "rl_version",
            "rl_get_mask", "rl_motion_x_noalloc", "rl_batch_create", "rl_batch_submit",
            "rl_batch_query", "rl_batch_wait", "rl_batch_sync", "rl_batch_destroy",
-           "rl_batch_last_error", "rl_iterate_tiles", "rl_selftest_wait_timeout")
+           "rl_batch_last_error", "rl_batch_cancel", "rl_iterate_tiles", "rl_selftest_wait_timeout",
+           "rl_test_fail_allocation")
 RL_NOALLOC_MAX_PIXELS = 4194304
 
 
@@ -131,6 +132,10 @@ def load() -> ctypes.CDLL:
     lib.rl_batch_destroy.argtypes = [P]
     lib.rl_batch_last_error.restype = ctypes.c_char_p
     lib.rl_batch_last_error.argtypes = [P]
+    lib.rl_batch_cancel.restype = ctypes.c_int
+    lib.rl_batch_cancel.argtypes = [P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+    lib.rl_test_fail_allocation.restype = None
+    lib.rl_test_fail_allocation.argtypes = [ctypes.c_int]
     lib.rl_iterate_tiles.restype = ctypes.c_int
     lib.rl_iterate_tiles.argtypes = [P, ctypes.POINTER(rl_job), ctypes.c_int]
     lib.rl_motion_x_noalloc.restype = ctypes.c_int
@@ -377,6 +382,14 @@ class Batch:
 
     def wait(self, ticket: int) -> None:
         self._check(load().rl_batch_wait(self.h, ticket))
+
+    def cancel(self, ticket: int) -> bool:
+        """Cancel a job; returns True if it was already on the GPU (it runs to
+        the end and its result is to be discarded), False if it was dropped
+        before it started."""
+        running = ctypes.c_int()
+        self._check(load().rl_batch_cancel(self.h, ticket, ctypes.byref(running)))
+        return bool(running.value)
 
     def sync(self) -> None:
         self._check(load().rl_batch_sync(self.h))
