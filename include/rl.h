@@ -140,6 +140,16 @@ typedef struct {
                                    sum path could keep whole rows resident
                                    for all iterations, or the disc path run
                                    them all in one persistent launch      */
+#define RL_FLAG_AUTOTUNE 8      /* choose the disc path's launch form, the
+                                   running-sum chunk width and the stencil
+                                   tile shape by timing the candidates on the
+                                   first call for a (site, PSF, size,
+                                   storage, boundary, thinning, SM count)
+                                   key -- that call blocks while it tunes --
+                                   and caching the fastest for the process
+                                   (and, with RL_TUNE_CACHE naming a file,
+                                   across processes as JSON lines); the
+                                   choice depends on the request alone    */
 #define RL_FLAG_PERSISTENT 4    /* disc path: one persistent launch for all
                                    iterations even where the image has too
                                    few tiles for it to pay (about one tile

@@ -179,9 +179,15 @@ __global__ void __launch_bounds__(256) k_motion_x_tb(IterArgs a, TBArgs tb, int 
 }
 
 // Chunk width, threads per row and rows per CTA of the resident kernel.
-inline int tb_chunk(int W) { return W <= 13 * 256 ? 13 : (W <= 17 * 256 ? 17 : 33); }
-inline void tb_shape(int W, int &tpr, int &rpc) {
-    const int chunks = (W + tb_chunk(W) - 1) / tb_chunk(W);
+// chunk = 0: the built-in table by row length; else 13, 17 or 33 (a tuned
+// choice).
+inline int tb_chunk(int W, int chunk = 0) {
+    if (chunk == 13 || chunk == 17 || chunk == 33) return chunk;
+    return W <= 13 * 256 ? 13 : (W <= 17 * 256 ? 17 : 33);
+}
+inline void tb_shape(int W, int chunk, int &tpr, int &rpc) {
+    const int ch = tb_chunk(W, chunk);
+    const int chunks = (W + ch - 1) / ch;
     tpr = ((chunks + 31) / 32) * 32;
     if (tpr > 256) tpr = 256;
     rpc = 256 / tpr;
@@ -191,7 +197,7 @@ template <typename T, bool THIN, int TCH>
 cudaError_t launch_x_tb_c(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
     const int L = a.ax + a.bx + 1;
     int tpr, rpc;
-    tb_shape(a.W, tpr, rpc);
+    tb_shape(a.W, TCH, tpr, rpc);
     const int line_floats = ((a.W + L - 1) + 3) & ~3;
     const int mask_bytes = THIN ? (a.W + 15) & ~15 : 0;
     const size_t smem = (size_t)rpc * (3 * line_floats * sizeof(float) + mask_bytes);
@@ -210,7 +216,7 @@ cudaError_t launch_x_tb_c(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
 
 template <typename T, bool THIN>
 cudaError_t launch_x_tb_t(const IterArgs &a, const TBArgs &tb, cudaStream_t s) {
-    switch (tb_chunk(a.W)) {
+    switch (tb_chunk(a.W, tb.chunk)) {
     case 13: return launch_x_tb_c<T, THIN, 13>(a, tb, s);
     case 17: return launch_x_tb_c<T, THIN, 17>(a, tb, s);
     default: return launch_x_tb_c<T, THIN, 33>(a, tb, s);

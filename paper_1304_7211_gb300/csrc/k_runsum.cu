@@ -233,15 +233,17 @@ cudaError_t launch_y_t(const IterArgs &a, cudaStream_t s) {
 
 }  // namespace
 
-size_t motion_x_tb_smem_bytes(int W, int L, bool thin) {
+size_t motion_x_tb_smem_bytes(int W, int L, bool thin, int chunk) {
     int tpr, rpc;
-    mtb::tb_shape(W, tpr, rpc);
+    mtb::tb_shape(W, chunk, tpr, rpc);
     const int line_floats = ((W + L - 1) + 3) & ~3;
     const int mask_bytes = thin ? (W + 15) & ~15 : 0;
     return (size_t)rpc * (3 * line_floats * sizeof(float) + mask_bytes);
 }
 
-bool motion_x_tb_fits(int W, int L, bool thin) { return motion_x_tb_smem_bytes(W, L, thin) <= 200 * 1024; }
+bool motion_x_tb_fits(int W, int L, bool thin, int chunk) {
+    return motion_x_tb_smem_bytes(W, L, thin, chunk) <= 200 * 1024;
+}
 
 cudaError_t launch_motion_x_tb(const IterArgs &a, const TBArgs &tb, int storage, bool thin,
                                cudaStream_t s) {

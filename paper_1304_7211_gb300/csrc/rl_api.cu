@@ -85,6 +85,11 @@ struct rl_ctx {
     int *pscratch = nullptr;
     size_t pscratch_bytes = 0;
     const int *pstatus = nullptr;  // status word of the last persistent launch, or NULL
+    // autotuner: the choice in effect for the current call at its tunable
+    // site (-1 = the built-in rule), and its scratch output
+    int tune_choice = -1;
+    void *tunebuf = nullptr;
+    size_t tunebuf_bytes = 0;
     void *tbuf[2] = {nullptr, nullptr};  // transposed f and u (motion along y)
     size_t tbuf_bytes = 0;
     void *tsched = nullptr;              // transposed schedule / mask bytes
@@ -297,6 +302,7 @@ static rl_status destroy_impl(rl_ctx *ctx) {
     cudaFree(ctx->zplane);
     cudaFree(ctx->tflags);
     cudaFree(ctx->pscratch);
+    cudaFree(ctx->tunebuf);
     cudaFree(ctx->tbuf[0]);
     cudaFree(ctx->tbuf[1]);
     cudaFree(ctx->tsched);
@@ -635,6 +641,7 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
     memset(&tb, 0, sizeof tb);
     tb.K = K;
     tb.round = ctx->storage != RL_STORAGE_F32;
+    tb.chunk = ctx->tune_choice > 0 ? ctx->tune_choice : 0;
     const bool ydir = ctx->axis == 1;
     const int Wt = ydir ? H : W, Ht = ydir ? W : H;   // the problem the kernel sees
     const long long tp = ((long long)Wt + 63) / 64 * 64;
@@ -869,9 +876,11 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     // 127 vs 137 us/it for r = 12 at 4096^2).
     const int tx = (W + rl::disc_tile() - 1) / rl::disc_tile(), ty = (H + rl::disc_tile() - 1) / rl::disc_tile();
     const long long slots = (long long)ctx->sms * rl::disc_min_blocks(R, false);
-    const bool persist_pays = 4LL * tx * ty >= 5LL * slots;  // at least 1.25 tiles per slot
+    // a tuned choice (0 = two launches, 1 = persistent) overrides the rule
+    const bool persist_pays = ctx->tune_choice >= 0 ? ctx->tune_choice == 1
+                                                    : 4LL * tx * ty >= 5LL * slots;  // at least 1.25 tiles per slot
     if (op == OP_DISC && !thin && !a.fold_ct && !(ctx->flags & RL_FLAG_PER_ITERATION) &&
-        (persist_pays || (ctx->flags & RL_FLAG_PERSISTENT))) {
+        (persist_pays || ((ctx->flags & RL_FLAG_PERSISTENT) && ctx->tune_choice < 0))) {
         const size_t n = (size_t)tx * ty + 2;  // progress per tile, ticket, status
         rl_status st = grow(ctx, (void **)&ctx->pscratch, &ctx->pscratch_bytes, n * sizeof(int),
                             "rl_iterate: tile progress");
@@ -972,7 +981,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     if (needs_fold(ctx) && ctx->kind == RL_PSF_MOTION && !(ctx->flags & RL_FLAG_PER_ITERATION)) {
         const int L = ctx->axis == 0 ? ctx->kw : ctx->kh;
         const int line = ctx->axis == 0 ? W : H;
-        if (rl::motion_x_tb_fits(line, L, thin != nullptr)) {
+        if (rl::motion_x_tb_fits(line, L, thin != nullptr, ctx->tune_choice > 0 ? ctx->tune_choice : 0)) {
             *path_out = RL_PATH_RUNSUM;
             return run_resident(ctx, f, start, u_out, W, H, pitch, K, thin, plane, sp);
         }
@@ -981,7 +990,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
     if (path == RL_PATH_RUNSUM && !(ctx->flags & RL_FLAG_PER_ITERATION)) {
         const int L = ctx->axis == 0 ? ctx->kw : ctx->kh;
         const int line = ctx->axis == 0 ? W : H;
-        if (rl::motion_x_tb_fits(line, L, thin != nullptr))
+        if (rl::motion_x_tb_fits(line, L, thin != nullptr, ctx->tune_choice > 0 ? ctx->tune_choice : 0))
             return run_resident(ctx, f, start, u_out, W, H, pitch, K, thin, plane, sp);
     }
     if ((K > 1 || u_out == start) && ctx->ubuf_bytes < plane * es) {
@@ -1054,7 +1063,10 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         a.relative = thin->relative != 0;
         a.tau = thin->threshold;
     }
-    const rl::TileShape ts = rl::tile_shape_for(a.ax, a.bx, a.ay, a.by);
+    // a tuned tile shape (tx << 16 | ty) overrides the table
+    const rl::TileShape ts = ctx->tune_choice > 0
+                                 ? rl::TileShape{ctx->tune_choice >> 16, ctx->tune_choice & 0xffff}
+                                 : rl::tile_shape_for(a.ax, a.bx, a.ay, a.by);
     int cur = 0;  // mask plane holding the current mask
     auto args_for = [&](int k) {
         IterArgs b = a;
@@ -1100,7 +1112,7 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         // plain RL: iterations 1 .. K-2 alternate the two scratch buffers,
         // so a segment of 10 repeats; replay it from a CUDA graph
         int kn = k;
-        st = run_segments(ctx, 1, K - 1, 10, 2 + path, issue, args_for, &kn);
+        st = run_segments(ctx, 1, K - 1, 10, (2 + path) | (ts.tx << 4) | (ts.ty << 16), issue, args_for, &kn);
         if (st != RL_OK) return st;
         ctx->launches += kn - k;
         k = kn;
@@ -1122,6 +1134,100 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
                                  cudaMemcpyDeviceToDevice, ctx->stream),
                "rl_iterate: copy out");
     }
+    return RL_OK;
+}
+
+
+// ---- autotuner -------------------------------------------------------------
+// The tunable site of a call, its candidates and its cache key.  Only choices
+// that leave the arithmetic of every pixel unchanged, or change it by FP32
+// rounding alone, are tuned: the disc path's launch form (bit-identical), the
+// running-sum chunk width (where the window sums restart) and the stencil
+// tile shape (bit-identical).
+struct TuneSite {
+    std::string key;
+    std::vector<int> candidates;
+};
+
+TuneSite tune_site(const rl_ctx *ctx, int W, int H, const rl_thinning *thin) {
+    TuneSite t;
+    if (ctx->flags & RL_FLAG_PER_ITERATION) return t;
+    const int path = choose_path(ctx, W);
+    char buf[192];
+    const char *sto = ctx->storage == RL_STORAGE_F32 ? "f32" : ctx->storage == RL_STORAGE_BF16 ? "bf16" : "f16";
+    const char *bnd = ctx->boundary == RL_BOUNDARY_CLAMP ? "clamp" : "mirror";
+    const char *th = thin ? (thin->schedule ? "replay" : "thin") : "plain";
+    if (ctx->kind == RL_PSF_MOTION && (path == RL_PATH_RUNSUM || needs_fold(ctx))) {
+        const int L = ctx->axis == 0 ? ctx->kw : ctx->kh;
+        const int line = ctx->axis == 0 ? W : H;
+        for (int c : {13, 17, 33})
+            if (rl::motion_x_tb_fits(line, L, thin != nullptr, c)) t.candidates.push_back(c);
+        snprintf(buf, sizeof buf, "motion-chunk:L%d%s:%dx%d:%s:%s:%s:sm%d", L, ctx->axis ? "y" : "x", W, H, sto,
+                 bnd, th, ctx->sms);
+    } else if (path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
+               ctx->disc_radius <= rl::kDiscMaxRadius && !thin && !needs_fold(ctx)) {
+        t.candidates = {0, 1};
+        snprintf(buf, sizeof buf, "disc-form:r%d:%dx%d:%s:%s:%s:sm%d", ctx->disc_radius, W, H, sto, bnd, th,
+                 ctx->sms);
+    } else if (path == RL_PATH_STENCIL && !ctx->sq_k) {
+        t.candidates = {64 << 16 | 32, 64 << 16 | 64, 128 << 16 | 32, 128 << 16 | 64};
+        snprintf(buf, sizeof buf, "stencil-tile:%dx%da%d,%d:%dx%d:%s:%s:%s:sm%d", ctx->kw, ctx->kh, ctx->ax, ctx->ay,
+                 W, H, sto, bnd, th, ctx->sms);
+    } else {
+        return t;
+    }
+    if (t.candidates.size() > 1) t.key = buf;
+    return t;
+}
+
+// With RL_FLAG_AUTOTUNE: the first call for a key times every candidate on
+// the call's own inputs (a warm-up run, then a timed run of up to 10
+// iterations, into library scratch; CUDA events on the context stream) and
+// caches the fastest; later calls with the key take the cached choice.
+rl_status tune_if_needed(rl_ctx *ctx, const void *f, const void *u0, int W, int H, long long pitch, int K,
+                         const rl_thinning *thin) {
+    ctx->tune_choice = -1;
+    if (!(ctx->flags & RL_FLAG_AUTOTUNE) || K < 1) return RL_OK;
+    const TuneSite site = tune_site(ctx, W, H, thin);
+    if (site.key.empty()) return RL_OK;
+    int choice = -1;
+    if (rl::tune_get(site.key, &choice)) {
+        ctx->tune_choice = choice;
+        return RL_OK;
+    }
+    const size_t bytes = (size_t)pitch * H * elem_size(ctx->storage);
+    rl_status st = grow(ctx, &ctx->tunebuf, &ctx->tunebuf_bytes, bytes, "rl_iterate: tuning buffer");
+    if (st != RL_OK) return st;
+    const int kt = K < 10 ? K : 10;
+    float best_ms = 0.f;
+    std::string times;
+    for (int c : site.candidates) {
+        ctx->tune_choice = c;
+        int path = 0;
+        float ms = -1.f;
+        st = run_device(ctx, f, u0, ctx->tunebuf, W, H, pitch, kt, thin, &path);  // warm-up
+        if (st == RL_OK) {
+            CK(cudaEventRecord(ctx->ev0, ctx->stream), "rl_iterate: tuning");
+            st = run_device(ctx, f, u0, ctx->tunebuf, W, H, pitch, kt, thin, &path);
+            CK(cudaEventRecord(ctx->ev1, ctx->stream), "rl_iterate: tuning");
+            CK(cudaEventSynchronize(ctx->ev1), "rl_iterate: tuning");
+            if (st == RL_OK) CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "rl_iterate: tuning");
+        }
+        if (st != RL_OK) {  // a candidate that cannot run here (shared memory) is skipped
+            CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: tuning");
+            (void)cudaGetLastError();
+        }
+        char b[32];
+        snprintf(b, sizeof b, "%s%.1f", times.empty() ? "" : " ", ms >= 0.f ? 1e3f * ms / kt : -1.f);
+        times += b;
+        if (ms >= 0.f && (choice < 0 || ms < best_ms)) {
+            best_ms = ms;
+            choice = c;
+        }
+    }
+    if (choice < 0) return fail(ctx, RL_ERR_CUDA, "rl_iterate: no tuning candidate ran");
+    rl::tune_put(site.key, choice, times);
+    ctx->tune_choice = choice;
     return RL_OK;
 }
 
@@ -1199,6 +1305,10 @@ static rl_status iterate_impl(rl_ctx *ctx, const void *f, const void *u0, void *
         df = ctx->stage[0];
         du = u0 ? ctx->stage[1] : nullptr;
         dout = ctx->stage[2];
+    }
+    {
+        rl_status st = tune_if_needed(ctx, df, du, W, H, dp, iterations, thin);
+        if (st != RL_OK) return st;
     }
     ctx->launches = 0;
     if (stats) CK(cudaEventRecord(ctx->ev0, ctx->stream), "rl_iterate: event");

@@ -232,6 +232,7 @@ struct TBArgs {
     long long s_pitch;      // row pitch of a schedule plane (bytes)
     long long s_plane;      // bytes per schedule plane
     int round;              // round u to the storage type after every iteration
+    int chunk;              // running-sum chunk width: 0 = built-in table, else 13 / 17 / 33
 };
 
 // Ratio f / v of Eq. 3 with q = 0 where the re-blurred value vanishes.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
 #include "rl_common.cuh"
 
 namespace rl {
@@ -21,8 +23,9 @@ bool motion_x_fits(int W, int L);
 // all tb.K iterations (one launch per rl_iterate call).
 cudaError_t launch_motion_x_tb(const IterArgs &a, const TBArgs &tb, int storage, bool thin,
                                cudaStream_t s);
-size_t motion_x_tb_smem_bytes(int W, int L, bool thin);
-bool motion_x_tb_fits(int W, int L, bool thin);
+// chunk: 0 = the built-in width for the row length, else 13, 17 or 33
+size_t motion_x_tb_smem_bytes(int W, int L, bool thin, int chunk = 0);
+bool motion_x_tb_fits(int W, int L, bool thin, int chunk = 0);
 // per storage type and thinning mode (k_motion_tb_*.cu)
 cudaError_t launch_motion_tb_f32(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
 cudaError_t launch_motion_tb_f32_thin(const IterArgs &a, const TBArgs &tb, cudaStream_t s);
@@ -169,4 +172,9 @@ cudaError_t launch_stencil_k5(const IterArgs &, const float *, int, bool, float 
 cudaError_t launch_stencil_k7(const IterArgs &, const float *, int, bool, float *, long long, cudaStream_t);
 cudaError_t launch_stencil_k9(const IterArgs &, const float *, int, bool, float *, long long, cudaStream_t);
 
+// Autotuner choice cache (rl_tune.cu): keyed by the request alone; backed by
+// the file named in RL_TUNE_CACHE (JSON lines) when that is set.
+bool tune_get(const std::string &key, int *choice);
+void tune_put(const std::string &key, int choice, const std::string &timings_us);
+void tune_clear();
 }  // namespace rl

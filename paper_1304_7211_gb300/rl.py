@@ -52,6 +52,7 @@ class rl_thinning(ctypes.Structure):
 RL_FLAG_PER_ITERATION = 1
 RL_FLAG_ADJOINT_TRANSPOSE = 2
 RL_FLAG_PERSISTENT = 4
+RL_FLAG_AUTOTUNE = 8
 ADJOINT = {"padflip": 0, "transpose": RL_FLAG_ADJOINT_TRANSPOSE}
 
 
