@@ -331,48 +331,56 @@ def run_case(args):
     return 0
 
 
-def batch_run(local, n_images=64, slots=32):
+def batch_run(local, n_images=64, slots=32, storage="f32"):
     """Batched workload: 64 images, sides log-uniform in [128, 1536], PSF and
     iteration count (50..300) per image, all submitted to one rl_batch
     (32 streams: small images fill few CTA slots each) vs the same solves one
-    at a time.  Returns a dict."""
+    at a time; the batch runs with the built-in launch choices and with the
+    autotuner's (its cache filled by a first, untimed pass).  Returns a
+    dict."""
     import numpy as np
     import torch
     from paper_1304_7211_gb300 import rl, synth
     dev = torch.device("cuda", local)
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[storage]
     jobs = []
     for (w, h, spec, its, seed) in synth.batch_specs(n_images):
         c = synth.batch_case(w, h, spec, its, seed)
-        f = torch.from_numpy(c.f.astype(np.float32)).to(dev)
+        f = torch.from_numpy(c.f.astype(np.float32)).to(dev).to(dt)
         jobs.append((spec, f, torch.empty_like(f), its, w, h))
     px_it = float(sum(w * h * its for (_, _, _, its, w, h) in jobs))
 
-    def batched():
-        with rl.Batch(slots, device=local) as b:
+    def batched(flags=0):
+        with rl.Batch(slots, device=local, storage=storage, flags=flags) as b:
             for spec, f, u, its, w, h in jobs:
                 b.submit(spec, f, u, its, w, h)
             b.sync()
 
+    def tuned():
+        batched(rl.RL_FLAG_AUTOTUNE)
+
     def sequential():
         for spec, f, u, its, w, h in jobs:
-            with rl.Deconvolver(spec, device=local) as d:
+            with rl.Deconvolver(spec, device=local, storage=storage) as d:
                 rl.rl_iterate(d.ctx, f, None, u, w, h, w, its)
         torch.cuda.synchronize(dev)
 
     batched()  # warm-up (scratch growth, module load)
+    tuned()    # fills the tuning cache for every job's key
     sequential()
     ts = {}
-    for name, fn in (("batched", batched), ("sequential", sequential)):
+    for name, fn in (("batched", batched), ("tuned", tuned), ("sequential", sequential)):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         fn()
         torch.cuda.synchronize(dev)
         ts[name] = time.perf_counter() - t0
     return {"workload": f"{n_images} images, sides log-uniform [128,1536], motion x/y 5-41, "
-                        f"disc r 3-15, gaussian 7x7; 50-300 it; fp32", "slots": slots,
-            "px_it": px_it, "batched_ms": 1e3 * ts["batched"],
+                        f"disc r 3-15, gaussian 7x7; 50-300 it; {storage}", "slots": slots,
+            "px_it": px_it, "batched_ms": 1e3 * ts["batched"], "tuned_ms": 1e3 * ts["tuned"],
             "sequential_ms": 1e3 * ts["sequential"],
-            "value": px_it / ts["batched"] / 1e6, "sequential_value": px_it / ts["sequential"] / 1e6,
+            "value": px_it / ts["batched"] / 1e6, "tuned_value": px_it / ts["tuned"] / 1e6,
+            "sequential_value": px_it / ts["sequential"] / 1e6,
             "speedup_vs_plain": ts["sequential"] / ts["batched"], "unit": UNIT,
             "timing": "host wall clock around submit..sync, inputs resident"}
 
@@ -428,43 +436,50 @@ def tiles_run(local, n_images=64, slots=32):
             "timing": "host wall clock around the call(s)..sync, inputs resident"}
 
 
-def serve_run(local, n=200, rate=100.0, slots=16):
-    """Served workload: a Poisson-arrival trace (rate req/s), sides
+def serve_run(local, n=400, rates=(100.0, 200.0), slots=16):
+    """Served workload: a Poisson-arrival trace of n requests, sides
     log-uniform in [256, 4096], PSF as in the batched workload, 50..500
     iterations, thinning threshold 1e-4 (mask recomputed every 10
-    iterations), admission under a 150 GB budget; compared with sequential
-    plain solves of the same requests.  Observed images are crops of four
-    pre-blurred 4096^2 images (the request's PSF still drives the solve)."""
+    iterations), admission under a 150 GB budget.  Each request's observed
+    image is its own latent crop blurred by its own PSF with Poisson noise,
+    made on the GPU before the run (it arrives on the device; the result goes
+    back to pinned host memory).  The same requests are served at every rate
+    (arrival times scale with 1 / rate).  Baseline: the plain path as a
+    server -- one request at a time in arrival order, each taking its
+    measured alone-time -- on the same trace.  Returns a dict."""
     import numpy as np
     from paper_1304_7211_gb300 import serve, synth
-    rng = np.random.default_rng(synth.SEED_BASE + 5)
-    bases = {}
-    for k, spec in enumerate((synth.motion(21, 0), synth.motion(21, 1), synth.disc(8),
-                              synth.gaussian(7, 1.5))):
-        bases[k] = synth.make_case(4096, 4096, spec, 0, "poisson", synth.SEED_BASE + 500 + k).f
-    reqs = []
-    for j, (t, w, h, spec, its, seed) in enumerate(synth.serve_trace(n, rate)):
-        fam = {"motion": spec.axis, "disc": 2, "dense": 3}[spec.kind]
-        y0 = int(rng.integers(0, 4096 - h + 1))
-        x0 = int(rng.integers(0, 4096 - w + 1))
-        f = bases[fam][y0:y0 + h, x0:x0 + w].astype(np.float32)
-        reqs.append(serve.Request(j, t, f, spec, its, (1e-4, True, 10, 10)))
+    trace = synth.serve_trace(n, 1.0)
+    fs = synth.serve_inputs_device(trace, local)
+    thin = (1e-4, True, 10, 10)
+
+    def requests(rate):
+        return [serve.Request(j, t / rate, f, spec, its, thin)
+                for j, ((t, w, h, spec, its, _), f) in enumerate(zip(trace, fs))]
+
+    alone = requests(1.0)
+    svc = serve.service_times(alone, device=local)
     srv = serve.Server(device=local, slots=slots, hbm_budget_bytes=150e9)
+    rows = []
     try:
-        warm = [serve.Request(-1, 0.0, r.f, r.spec, 5, r.thin) for r in reqs[:8]]
-        srv.run(warm, realtime=False)
-        rep = srv.run(reqs, realtime=True)
+        srv.run([serve.Request(-1, 0.0, r.f, r.spec, 5, r.thin) for r in alone[:8]], realtime=False)
+        for rate in rates:
+            reqs = requests(rate)
+            rep = srv.run(reqs, realtime=True)
+            fifo = serve.fifo_report(reqs, svc)
+            same = sum(bool(np.array_equal(r.result, a.result)) for r, a in zip(reqs, alone))
+            rows.append({"rate_per_s": rate, "served": rep.as_dict(), "fifo_sequential": fifo.as_dict(),
+                         "served_over_sequential": rep.mpx_it_per_s / fifo.mpx_it_per_s,
+                         "results_bitwise_same_as_alone": f"{same}/{len(reqs)}"})
     finally:
         srv.close()
-    seq_s = serve.sequential(reqs, device=local)
-    d = rep.as_dict()
-    d.update({"rate_per_s": rate, "slots": slots, "unit": UNIT, "value": rep.mpx_it_per_s,
-              "sequential_value": rep.px_it / seq_s / 1e6,
-              "sequential_s": seq_s,
-              "inputs": "crops of 4 pre-blurred 4096^2 images; request PSF drives the solve",
-              "workload": f"{n} requests, Poisson arrivals {rate}/s, sides log-uniform "
-                          f"[256,4096], 50-500 it, thinning 1e-4 (P=Q=10), budget 150 GB"})
-    return d
+    px_it = float(sum(r.f.shape[0] * r.f.shape[1] * r.iterations for r in alone))
+    return {"workload": f"{n} requests, Poisson arrivals, sides log-uniform [256,4096], motion x/y 5-41, "
+                        f"disc r 3-15, gaussian 7x7, 50-500 it, thinning 1e-4 (P=Q=10), budget 150 GB, "
+                        f"{slots} streams; fp32",
+            "unit": UNIT, "px_it": px_it, "sequential_offline_value": px_it / sum(svc) / 1e6,
+            "inputs": "per request: crop of a seeded 4096^2 latent, blurred by its own PSF, Poisson peak 1000",
+            "rates": rows}
 
 
 def thinned_run(local, size=4096, iters=300, oracle_size=384):
@@ -606,9 +621,11 @@ def main():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the served sub-measurement")
-    ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--workload", default="plain", choices=["plain", "thinned"],
-                    help="'thinned' prints the thinned-workload table instead of the bench line")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--workload", default="plain", choices=["plain", "thinned", "serve"],
+                    help="'thinned' prints the thinned-workload table, 'serve' the full served "
+                         "workload (2000 requests at 20 / 50 / 100 / 200 per second), instead of "
+                         "the bench line")
     ap.add_argument("--no-config3", action="store_true", help="skip the 4096^2 thinned sub-measurement")
     ap.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "COMMAND"), default=None,
                     help="write profiles/traffic_plain_2048.json from an ncu CSV (launch list with "
@@ -623,12 +640,14 @@ def main():
         return run_reference(args, ws, rank)
     if args.case:
         return run_case(args)
-    if args.workload == "thinned":
+    if args.workload in ("thinned", "serve"):
         import torch
         torch.cuda.set_device(local)
         from paper_1304_7211_gb300 import _build
         _build.build()
-        print(json.dumps(thinned_run(local)), flush=True)
+        out = (thinned_run(local) if args.workload == "thinned"
+               else serve_run(local, n=2000, rates=(20.0, 50.0, 100.0, 200.0)))
+        print(json.dumps(out), flush=True)
         return 0
 
     import numpy as np
@@ -751,6 +770,7 @@ def main():
     line["config1"] = config1_run(local)
     if not args.no_batch:
         line["batch"] = batch_run(local)
+        line["batch_bf16"] = batch_run(local, storage="bf16")
         line["batch_tiles"] = tiles_run(local)
     if not args.no_config3 and ws == 1:
         line["config3"] = thinned_run(local)

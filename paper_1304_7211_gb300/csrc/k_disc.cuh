@@ -1086,8 +1086,10 @@ cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cuda
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disc_persist<T, Op>, 128, smem)) != cudaSuccess)
         return e;
     if (occ < 1) return cudaErrorNotSupported;
-    const long long n_items = 2LL * p.K * p.tiles_x * p.tiles_y;
-    const long long grid = std::min<long long>((long long)occ * sms, n_items);
+    // no more CTAs than tiles: a half has one item per tile, so extra CTAs
+    // would only wait -- and a small image then leaves the other SMs to the
+    // other streams of a batch
+    const long long grid = std::min<long long>((long long)occ * sms, (long long)p.tiles_x * p.tiles_y);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(128);

@@ -1181,9 +1181,10 @@ TuneSite tune_site(const rl_ctx *ctx, int W, int H, const rl_thinning *thin) {
 }
 
 // With RL_FLAG_AUTOTUNE: the first call for a key times every candidate on
-// the call's own inputs (a warm-up run, then a timed run of up to 10
-// iterations, into library scratch; CUDA events on the context stream) and
-// caches the fastest; later calls with the key take the cached choice.
+// the call's own inputs (a warm-up run, then the faster of two timed runs of
+// up to 10 iterations, into library scratch; CUDA events on the context
+// stream) and caches the fastest; later calls with the key take the cached
+// choice.  In a batch the timing shares the GPU with the other streams.
 rl_status tune_if_needed(rl_ctx *ctx, const void *f, const void *u0, int W, int H, long long pitch, int K,
                          const rl_thinning *thin) {
     ctx->tune_choice = -1;
@@ -1206,12 +1207,14 @@ rl_status tune_if_needed(rl_ctx *ctx, const void *f, const void *u0, int W, int 
         int path = 0;
         float ms = -1.f;
         st = run_device(ctx, f, u0, ctx->tunebuf, W, H, pitch, kt, thin, &path);  // warm-up
-        if (st == RL_OK) {
+        for (int rep = 0; rep < 2 && st == RL_OK; ++rep) {  // the faster of two timed runs
             CK(cudaEventRecord(ctx->ev0, ctx->stream), "rl_iterate: tuning");
             st = run_device(ctx, f, u0, ctx->tunebuf, W, H, pitch, kt, thin, &path);
             CK(cudaEventRecord(ctx->ev1, ctx->stream), "rl_iterate: tuning");
             CK(cudaEventSynchronize(ctx->ev1), "rl_iterate: tuning");
-            if (st == RL_OK) CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "rl_iterate: tuning");
+            float t = 0.f;
+            if (st == RL_OK) CK(cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1), "rl_iterate: tuning");
+            if (st == RL_OK && (ms < 0.f || t < ms)) ms = t;
         }
         if (st != RL_OK) {  // a candidate that cannot run here (shared memory) is skipped
             CK(cudaStreamSynchronize(ctx->stream), "rl_iterate: tuning");

@@ -240,3 +240,40 @@ def serve_trace(n: int = 2000, rate: float = 100.0, lo: int = 256,
         its = int(rng.integers(it_lo, it_hi + 1))
         out.append((t, w, h, spec, its, seed + 100000 + j))
     return out
+
+
+def serve_inputs_device(trace, device: int = 0, bases: int = 4, base_size: int = 4096,
+                        peak: float = 1000.0, seed: int = SEED_BASE + 6):
+    """Observed images of a served trace, made on the GPU: request j's latent
+    image is a crop of one of `bases` seeded 4096^2 latent images, blurred
+    by the request's own PSF (Eq. 1, with the half-sample mirror continuation)
+    and given Poisson noise at `peak` counts.  Returns float32 CUDA tensors.
+    The blur is torch's library convolution: these are benchmark inputs, not
+    reference values."""
+    import torch
+    import torch.nn.functional as F
+    dev = torch.device("cuda", device)
+    lat = [torch.from_numpy(latent_image(base_size, base_size, seed + k).astype(np.float32)).to(dev)
+           for k in range(bases)]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    rng = np.random.default_rng(seed)
+    out = []
+    for j, (_, w, h, spec, _, _) in enumerate(trace):
+        g = lat[j % bases]
+        y0 = int(rng.integers(0, base_size - h + 1))
+        x0 = int(rng.integers(0, base_size - w + 1))
+        crop = g[y0:y0 + h, x0:x0 + w][None, None]
+        taps = torch.from_numpy(np.ascontiguousarray(spec.dense()[::-1, ::-1]).astype(np.float32)).to(dev)
+        kh, kw = taps.shape
+        py, px = kh // 2, kw // 2
+        # half-sample mirror: ... c b a | a b c ...
+        x = torch.cat([crop[..., :, :px].flip(-1), crop, crop[..., :, w - (kw - 1 - px):].flip(-1)], dim=-1) \
+            if kw > 1 else crop
+        x = torch.cat([x[..., :py, :].flip(-2), x, x[..., h - (kh - 1 - py):, :].flip(-2)], dim=-2) \
+            if kh > 1 else x
+        b = F.conv2d(x, taps[None, None])[0, 0]
+        scale = peak / 250.0
+        f = torch.poisson(torch.clamp(b, min=0.0) * scale, generator=gen) / scale
+        out.append(f.contiguous())
+    return out
