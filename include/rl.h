@@ -83,7 +83,12 @@ typedef enum {
                             or dense taps that are uniform with one contiguous
                             run per row); separable sliding sums for a uniform
                             rectangle reaching up to 16 pixels from the anchor  */
-    RL_PATH_STENCIL = 3  /* direct summation over the non-zero taps (any PSF)     */
+    RL_PATH_STENCIL = 3, /* direct summation over the non-zero taps (any PSF)     */
+    RL_PATH_SAT = 4      /* uniform rectangles reaching up to 16 pixels from the
+                            anchor only: the summed-area table (2D cumulated
+                            sums, Sec. 3), four lookups per output in 64-bit
+                            fixed point; no thinning.  AUTO never picks it:
+                            the separable sums of SPAN are faster            */
 } rl_path;
 
 /*

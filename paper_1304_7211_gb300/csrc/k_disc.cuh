@@ -101,14 +101,15 @@ __device__ __forceinline__ float gld_elem(const T *p, long long i) {
 // 4-byte copies of the boundary-mapped pixels; the caller waits
 // (cp_async_wait_all) before the barrier.  16-bit storage goes through
 // registers, converted to FP32, several units in flight per thread.
-template <typename T, int nrows, int nu, int pitch, bool COH = false>
+template <typename T, int nrows, int nu, int pitch, bool COH = false, int NT = 128>
 __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, int y0, int xs, const T *src,
                                            long long sp, int tid) {
     constexpr int total = nrows * nu;
     if constexpr (sizeof(T) == 4) {
         const float *s = reinterpret_cast<const float *>(src);
-        // Interior tile with 16-byte aligned rows: warp w copies rows w, w + 4,
-        // ..., lane l units l and l + 32 of each (nu <= 64), no boundary map.
+        // Interior tile with 16-byte aligned rows: warp w copies rows w, w +
+        // NT / 32, ..., lane l units l and l + 32 of each (nu <= 64), no
+        // boundary map.
         static_assert(nu <= 64, "two units per lane");
         if (y0 >= 0 && y0 + nrows <= H && xs >= 0 && xs + 4 * nu <= W &&
             ((reinterpret_cast<uintptr_t>(s) | (uintptr_t)(sp * 4)) & 15) == 0) {
@@ -119,17 +120,18 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
                 if (u < nu) {
                     const float *g = s + (long long)(y0 + w) * sp + xs + 4 * u;
                     float *d = dst + w * pitch + (hunit(u) << 2);
+                    constexpr int NW = NT / 32;
 #pragma unroll 4
-                    for (int r = w; r < nrows; r += 4) {
+                    for (int r = w; r < nrows; r += NW) {
                         cp_async16(d, g);
-                        g += 4 * sp;
-                        d += 4 * pitch;
+                        g += NW * sp;
+                        d += NW * pitch;
                     }
                 }
             }
             return;
         }
-        for (int e = tid; e < total; e += 128) {
+        for (int e = tid; e < total; e += NT) {
             const int r = e / nu, u = e - r * nu;
             const int yy = bmap(y0 + r, H, clamp);
             const float *srow = s + (long long)yy * sp;
@@ -148,11 +150,11 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
         return;
     }
     constexpr int B = 4;
-    for (int e0 = tid; e0 < total; e0 += 128 * B) {
+    for (int e0 = tid; e0 < total; e0 += NT * B) {
         float v[B][4];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            const int e = e0 + 128 * b;
+            const int e = e0 + NT * b;
             if (e < total) {
                 const int r = e / nu, u = e - r * nu;
                 const T *srow = src + (long long)bmap(y0 + r, H, clamp) * sp;
@@ -181,7 +183,7 @@ __device__ __forceinline__ void stage_halo(float *dst, int clamp, int W, int H, 
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            const int e = e0 + 128 * b;
+            const int e = e0 + NT * b;
             if (e < total) {
                 const int r = e / nu, u = e - r * nu;
                 *reinterpret_cast<float4 *>(dst + r * pitch + (hunit(u) << 2)) =
@@ -269,16 +271,16 @@ __device__ __forceinline__ void f2add(unsigned long long &acc, unsigned long lon
 // them make the row pitch an odd number of units, so the prefix pass (one
 // thread per row, all at the same unit) puts 8 consecutive rows on 8
 // distinct bank quads.
-template <int R, int TXg = TX>
-using DiscHalo = Halo<R, 3, TXg>;
+template <int R, int TXg = TX, int TYg = TY>
+using DiscHalo = Halo<R, 3, TXg, TYg>;
 
 // Exclusive prefix of every staged row, in place: logical column k of a row
 // (0 <= k <= 4 NU, the last in the spare unit) becomes the sum of columns
 // [0, k).  One thread per row, a unit at a time.
-template <int R, int TXg>
+template <int R, int TXg, int TYg, int NT>
 __device__ __forceinline__ void row_prefix(float *tile) {
-    using G = DiscHalo<R, TXg>;
-    static_assert(G::NR <= 128, "one thread per staged row");
+    using G = DiscHalo<R, TXg, TYg>;
+    static_assert(G::NR <= NT, "one thread per staged row");
     if (threadIdx.x < G::NR) {
         float *row = tile + threadIdx.x * G::HP;
         float acc = 0.f;
@@ -376,9 +378,9 @@ __device__ __forceinline__ void load_needed(const float *const (&up)[WinUnits<R,
     }
 }
 
-template <int R, int TXg, int SYb>
+template <int R, int TXg, int TYg, int SYb>
 __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, float (&out)[SYb][SX]) {
-    using G = DiscHalo<R, TXg>;
+    using G = DiscHalo<R, TXg, TYg>;
     using N = DiscNeed<R, SYb>;
     constexpr int NP = N::NP;  // prefix entries in a block's window
     constexpr int NR = N::NR;
@@ -437,7 +439,10 @@ __device__ __forceinline__ void disc_block(const float *tile, int row0, int bx, 
 // without these members use the default 64 x 64 tile and 4-row blocks.
 struct DefaultGeo {
     static constexpr int kTX = TX, kTY = TY, kSY = SY;
+    static constexpr int kNT = 128;
     static constexpr bool kWide = false;
+    static constexpr bool kDefaultTile = true;
+    static constexpr int kMinBlocks = 0;  // 0: the register cap of the table below
 };
 
 // The disc on a TXg x 64 tile with SYb-row blocks.  Every form of the path
@@ -445,24 +450,27 @@ struct DefaultGeo {
 // entries once for 8 output rows instead of 4 -- a third fewer shared-memory
 // wavefronts per output -- but needs 126-166 registers, leaves 12-16 warps
 // per SM and measured slower at every size and radius tried.
-template <int R, int TXg = TX, int SYb = SY>
+template <int R, int TXg = TX, int SYb = SY, int TYg = TY>
 struct DiscOp {
     static constexpr int kR = R;
-    static constexpr int kTX = TXg, kTY = TY, kSY = SYb;
+    static constexpr int kTX = TXg, kTY = TYg, kSY = SYb;
+    static constexpr int kNT = TXg / SX * (TYg / SYb);  // one block per thread
     static constexpr bool kWide = TXg != TX;
-    using Geom = DiscHalo<R, TXg>;
+    static constexpr bool kDefaultTile = TXg == TX && TYg == TY && SYb == SY;
+    static constexpr int kMinBlocks = 0;
+    using Geom = DiscHalo<R, TXg, TYg>;
     static constexpr bool kUniform = true;
     static constexpr bool kPrepass = true;
     static constexpr int kExtraFloats = 0;
     struct Params {};
     template <bool FWD>
     static __device__ __forceinline__ void prepass(float *tile, float *, const Params &) {
-        row_prefix<R, TXg>(tile);
+        row_prefix<R, TXg, TYg, kNT>(tile);
     }
     template <bool FWD>
     static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SYb][SX],
                                                  const Params &) {
-        disc_block<R, TXg, SYb>(tile, row0, bx, acc);  // symmetric: forward = adjoint
+        disc_block<R, TXg, TYg, SYb>(tile, row0, bx, acc);  // symmetric: forward = adjoint
     }
 };
 
@@ -629,6 +637,108 @@ struct RectOp : DefaultGeo {
     }
 };
 
+// Uniform rectangle by a summed-area table (Sec. 3, rectangular blur: the
+// 2D cumulated sums, four lookups per output whatever the rectangle's size).
+// An FP32 table over a staged tile reaches thousands of times a pixel value,
+// so a small rectangle's sum -- a difference of four entries -- would lose
+// about ten bits.  The table is built instead in 64-bit fixed point: every
+// staged value is scaled by a power of two 2^e chosen per tile (the largest
+// with max|v| 2^e (rows x columns) < 2^62) and rounded to an integer, after
+// which every prefix sum and every box sum is exact; the only roundings are
+// that conversion (2^-e absolute) and the final conversion back to FP32.
+template <int R>
+struct SatOp : DefaultGeo {
+    static constexpr int kR = R;
+    using Geom = Halo<R>;
+    using G = Geom;
+    static constexpr bool kUniform = true;
+    static constexpr bool kPrepass = true;
+    static constexpr int NC = 4 * G::NU;  // logical staged columns
+    static constexpr int SR = G::NR + 1, SC = NC + 1;
+    // table pitch (in 64-bit entries): room for one entry of skew per 8
+    // columns, and = 2 (mod 4) so that the rows 4 apart of a 16-lane phase
+    // land on complementary banks
+    static constexpr int SCP = ((SC + SC / 8 + 1) + 3) / 4 * 4 + 2;
+    static constexpr int kExtraFloats = 2 * (SR * SCP + 2);  // the table, then the scale
+    // the table (61 KB at R = 8, 89 KB at R = 16) leaves room for two CTAs
+    // per SM, one at R = 16: no point capping registers for more
+    static constexpr int kMinBlocks = R > 8 ? 1 : 2;
+    struct Params { int lox, hix, loy, hiy; };
+    static __device__ __forceinline__ int sidx(int m, int c) { return m * G::HP + (hunit(c >> 2) << 2) + (c & 3); }
+    static __device__ __forceinline__ int tidx(int r, int c) { return r * SCP + c + (c >> 3); }
+
+    template <bool FWD>
+    static __device__ __forceinline__ void prepass(float *tile, float *extra, const Params &) {
+        long long *S = reinterpret_cast<long long *>(extra);
+        float *scale = reinterpret_cast<float *>(S + SR * SCP);
+        __shared__ float wmax[4];
+        // the largest magnitude in the staged tile
+        float m = 0.f;
+        for (int e = threadIdx.x; e < G::NR * NC; e += 128) m = fmaxf(m, fabsf(tile[sidx(e / NC, e % NC)]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const float mx = fmaxf(fmaxf(wmax[0], wmax[1]), fmaxf(wmax[2], wmax[3]));
+            // max |v| 2^e G::NR NC < 2^62
+            int e = 40;
+            if (mx > 0.f) {
+                int ex;
+                frexpf(mx * (float)(G::NR * NC), &ex);  // 2^(ex - 1) <= mx NR NC < 2^ex
+                e = min(40, 62 - ex);
+            }
+            scale[0] = ldexpf(1.f, e);
+            scale[1] = ldexpf(1.f, -e);
+        }
+        __syncthreads();
+        const float up = scale[0];
+        // row prefix sums, one thread per staged row; row 0 and column 0 are 0
+        if (threadIdx.x < G::NR) {
+            const int r = threadIdx.x;
+            long long acc = 0;
+            S[tidx(r + 1, 0)] = 0;
+            for (int c = 0; c < NC; ++c) {
+                acc += __float2ll_rn(tile[sidx(r, c)] * up);
+                S[tidx(r + 1, c + 1)] = acc;
+            }
+        }
+        for (int c = threadIdx.x; c < SC; c += 128) S[tidx(0, c)] = 0;
+        __syncthreads();
+        // then down the columns, one thread per column
+        for (int c = threadIdx.x; c < SC; c += 128) {
+            long long acc = 0;
+            for (int r = 1; r < SR; ++r) {
+                acc += S[tidx(r, c)];
+                S[tidx(r, c)] = acc;
+            }
+        }
+    }
+
+    // forward: v(p) = sum_t u(p - t), rows p.y - hiy .. p.y - loy and columns
+    // p.x - hix .. p.x - lox; adjoint: c(p) = sum_t q(p + t)
+    template <bool FWD>
+    static __device__ __forceinline__ void block(const float *tile, int row0, int bx, float (&acc)[SY][SX],
+                                                 const Params &p) {
+        const long long *S = reinterpret_cast<const long long *>(tile + G::NR * G::HP);
+        const float down = reinterpret_cast<const float *>(S + SR * SCP)[1];
+        const int ylo = FWD ? -p.hiy : p.loy, yhi = FWD ? -p.loy : p.hiy;
+        const int xlo = FWD ? -p.hix : p.lox, xhi = FWD ? -p.lox : p.hix;
+#pragma unroll
+        for (int i = 0; i < SY; ++i) {
+            const int r = row0 + i + R;  // staged row of the output
+            const int a0 = r + ylo, a1 = r + yhi + 1;
+#pragma unroll
+            for (int j = 0; j < SX; ++j) {
+                const int c = bx * SX + j + G::R4;  // staged column of the output
+                const int b0 = c + xlo, b1 = c + xhi + 1;
+                const long long sum = S[tidx(a1, b1)] - S[tidx(a0, b1)] - S[tidx(a1, b0)] + S[tidx(a0, b0)];
+                acc[i][j] = __ll2float_rn(sum) * down;
+            }
+        }
+    }
+};
+
 // Dense K x K taps centred on the origin (naive spatial convolution / list
 // filter of Sec. 3 and 5): every tap is a compile-time offset into the
 // register window and a constant-bank operand of its FMA.
@@ -776,7 +886,12 @@ constexpr int min_blocks() { return disc_min_blocks(R, THIN); }
 // A wide disc tile (8 x 8 blocks, 64 accumulators per thread) fits four
 // CTAs per SM up to R = 8 (its staged tile is 50 KB), three beyond.
 template <typename Op, bool THIN>
-constexpr int op_min_blocks() { return Op::kWide ? (Op::kR > 8 ? 3 : 4) : min_blocks<Op::kR, THIN>(); }
+constexpr int op_min_blocks() {
+    // the register cap of the 128-thread tile, for any number of threads
+    if constexpr (Op::kWide) return Op::kR > 8 ? 3 : 4;
+    else if constexpr (Op::kDefaultTile && Op::kMinBlocks > 0) return Op::kMinBlocks;
+    else return min_blocks<Op::kR, THIN>() * 128 / Op::kNT;
+}
 
 // One output tile (tbx, tby) of a half-iteration (Op::kTX x Op::kTY, blocks
 // of Op::kSY x SX), run by the whole CTA; the kernels below call it once per
@@ -787,9 +902,10 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     constexpr int R = Op::kR;
     constexpr int GTX = Op::kTX, GTY = Op::kTY, GSY = Op::kSY;
     constexpr int NBX = GTX / SX;  // block columns of the tile
+    constexpr int NT = Op::kNT;    // threads of the CTA
     static_assert(NBX % 8 == 0 && (GTY / GSY) % 4 == 0, "a warp covers 8 x 4 blocks");
-    static_assert(NBX * (GTY / GSY) == 128, "one block per thread");
-    static_assert(!(THIN && Op::kWide), "selective convolution uses the default tile (tile flags)");
+    static_assert(NBX * (GTY / GSY) == NT && NT % 32 == 0, "one block per thread");
+    static_assert(!THIN || Op::kDefaultTile, "selective convolution uses the default tile (tile flags)");
     using G = typename Op::Geom;
     extern __shared__ float sm[];
     const int x0 = tbx * GTX, y0 = tby * GTY;
@@ -801,10 +917,10 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + tby * a.tiles_x + tbx : nullptr;
     if (tflag && !a.full && *tflag == 0) return;
     if (FWD)
-        stage_halo<T, G::NR, G::NU, G::HP, COH>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
+        stage_halo<T, G::NR, G::NU, G::HP, COH, NT>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
                                     threadIdx.x);
     else
-        stage_halo<float, G::NR, G::NU, G::HP, COH>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
+        stage_halo<float, G::NR, G::NU, G::HP, COH, NT>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, qplane, q_pitch,
                                         threadIdx.x);
     {
         // The epilogue reads f (forward) or u (adjoint) at the tile's pixels:
@@ -812,7 +928,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         // blocks are summed.  Entry e covers 128 bytes of tile row e / L.
         constexpr int L = (GTX * (int)sizeof(T) + 127) / 128;  // 128-byte lines per tile row
 #pragma unroll
-        for (int e = threadIdx.x; e < GTY * L; e += 128) {
+        for (int e = threadIdx.x; e < GTY * L; e += NT) {
             const int y = y0 + e / L, x = x0 + (e % L) * (128 / (int)sizeof(T));
             if (y < a.H && x < a.W) {
                 const T *p = FWD ? (const T *)a.f + (long long)y * a.f_pitch + x
@@ -860,7 +976,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
         __syncthreads();
     }
 #pragma unroll 1
-    for (int e = threadIdx.x; e < n_active; e += 128) {
+    for (int e = threadIdx.x; e < n_active; e += NT) {
         int bx = nbx, by = nby;
         if (THIN && !a.full) {
             const int b = blist[e];
@@ -973,7 +1089,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
 }
 
 template <typename T, bool THIN, typename Op, bool FWD>
-__global__ void __launch_bounds__(128, op_min_blocks<Op, THIN>())
+__global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, THIN>())
     k_disc_half(const __grid_constant__ IterArgs a, const __grid_constant__ typename Op::Params prm, float *qplane,
                 long long q_pitch) {
     // Programmatic dependent launch: this grid may start while the previous
@@ -990,7 +1106,7 @@ __global__ void __launch_bounds__(128, op_min_blocks<Op, THIN>())
 // ones (phase 1).  Jobs of one launch share the block operation; FP32
 // storage, no thinning.
 template <typename Op, bool FWD>
-__global__ void __launch_bounds__(128, op_min_blocks<Op, false>())
+__global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
     k_disc_half_tiles(const TileJob *jobs, const int2 *items, int phase,
                       const __grid_constant__ typename Op::Params prm) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -1035,7 +1151,7 @@ __device__ __forceinline__ bool wait_tile(const int *w, int need, int *status, u
 }
 
 template <typename T, typename Op>
-__global__ void __launch_bounds__(128, op_min_blocks<Op, false>())
+__global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
     k_disc_persist(const __grid_constant__ PersistArgs p, const __grid_constant__ typename Op::Params prm) {
     __shared__ int s_item;
     const int n_tiles = p.tiles_x * p.tiles_y;
@@ -1083,7 +1199,8 @@ cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cuda
     int dev = 0, sms = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disc_persist<T, Op>, 128, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disc_persist<T, Op>, Op::kNT, smem)) !=
+        cudaSuccess)
         return e;
     if (occ < 1) return cudaErrorNotSupported;
     // no more CTAs than tiles: a half has one item per tile, so extra CTAs
@@ -1092,7 +1209,7 @@ cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cuda
     const long long grid = std::min<long long>((long long)occ * sms, (long long)p.tiles_x * p.tiles_y);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(128);
+    cfg.blockDim = dim3(Op::kNT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1122,7 +1239,7 @@ cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float 
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((a.W + Op::kTX - 1) / Op::kTX, (a.H + Op::kTY - 1) / Op::kTY);
-    cfg.blockDim = dim3(128);
+    cfg.blockDim = dim3(Op::kNT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1147,7 +1264,7 @@ cudaError_t launch_op_tiles(const TileJob *jobs, const int2 *items, int n_items,
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_items);
-    cfg.blockDim = dim3(128);
+    cfg.blockDim = dim3(Op::kNT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1218,6 +1335,16 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
                                  cudaStream_t s) {                                           \
         return disc::launch_op<disc::RectOp<R>>(a, {lox, hix, loy, hiy}, storage, thin,      \
                                                 qplane, q_pitch, s);                         \
+    }                                                                                        \
+    }
+
+#define RL_SAT_TU(R)                                                                         \
+    namespace rl {                                                                           \
+    cudaError_t launch_sat_r##R(const IterArgs &a, int lox, int hix, int loy, int hiy,       \
+                                int storage, float *qplane, long long q_pitch,               \
+                                cudaStream_t s) {                                            \
+        return disc::launch_op_t<disc::SatOp<R>, false>(a, {lox, hix, loy, hiy}, storage,    \
+                                                        qplane, q_pitch, s);                 \
     }                                                                                        \
     }
 

@@ -220,7 +220,7 @@ static rl_status create_impl(const rl_config *cfg, rl_ctx **out) {
     if (cfg) c = *cfg;
     if (c.storage < RL_STORAGE_F32 || c.storage > RL_STORAGE_F16 ||
         (c.boundary != RL_BOUNDARY_MIRROR && c.boundary != RL_BOUNDARY_CLAMP) ||
-        c.path < RL_PATH_AUTO || c.path > RL_PATH_STENCIL) {
+        c.path < RL_PATH_AUTO || c.path > RL_PATH_SAT) {
         g_create_error = "rl_create: unknown storage, boundary or path value";
         return RL_ERR_INVALID_ARG;
     }
@@ -747,7 +747,7 @@ rl_status run_resident(rl_ctx *ctx, const void *f, const void *start, void *u_ou
 }
 
 // Block operations of the two-half kernels.
-enum HalfOp { OP_DISC = 0, OP_BOX = 1, OP_STENCIL = 2, OP_RECT = 3 };
+enum HalfOp { OP_DISC = 0, OP_BOX = 1, OP_STENCIL = 2, OP_RECT = 3, OP_SAT = 4 };
 
 // Disc / box / register-stencil path: two launches per iteration (forward +
 // ratio, adjoint + update).  The adjoint half reads u only at its own pixels,
@@ -757,7 +757,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
                    long long pitch, int K, const rl_thinning *thin, long long sp, int op) {
     const int R = op == OP_STENCIL ? ctx->sq_k / 2
                   : op == OP_BOX   ? ctx->box_radius
-                  : op == OP_RECT  ? rl::rect_halo(std::max(std::max(std::abs(ctx->rect_lox), std::abs(ctx->rect_hix)),
+                  : (op == OP_RECT || op == OP_SAT) ? rl::rect_halo(std::max(std::max(std::abs(ctx->rect_lox), std::abs(ctx->rect_hix)),
                                                             std::max(std::abs(ctx->rect_loy), std::abs(ctx->rect_hiy))))
                                    : ctx->disc_radius;
     const size_t es = elem_size(ctx->storage);
@@ -861,6 +861,8 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
             op == OP_STENCIL ? rl::launch_stencil(b, ctx->sq_taps.data(), ctx->sq_k, ctx->storage, thin != nullptr,
                                                   ctx->qplane, sp, ctx->stream)
             : op == OP_BOX   ? rl::launch_box(b, ctx->storage, thin != nullptr, R, ctx->qplane, sp, ctx->stream)
+            : op == OP_SAT   ? rl::launch_sat(b, ctx->rect_lox, ctx->rect_hix, ctx->rect_loy, ctx->rect_hiy,
+                                              ctx->storage, ctx->qplane, sp, ctx->stream)
             : op == OP_RECT  ? rl::launch_rect(b, ctx->rect_lox, ctx->rect_hix, ctx->rect_loy, ctx->rect_hiy,
                                                ctx->storage, thin != nullptr, ctx->qplane, sp, ctx->stream)
                              : rl::launch_disc(b, ctx->storage, thin != nullptr, R, ctx->qplane, sp, ctx->stream);
@@ -874,7 +876,8 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     // at about one tile per CTA slot the two launches per iteration are
     // faster (measured: 41.5 vs 38.5 us/it for the disc r = 8 at 2048^2,
     // 127 vs 137 us/it for r = 12 at 4096^2).
-    const int tx = (W + rl::disc_tile() - 1) / rl::disc_tile(), ty = (H + rl::disc_tile() - 1) / rl::disc_tile();
+    const int tx = (W + rl::disc_tile() - 1) / rl::disc_tile();
+    const int ty = (H + rl::disc_persist_tile_h() - 1) / rl::disc_persist_tile_h();  // persistent tiles
     const long long slots = (long long)ctx->sms * rl::disc_min_blocks(R, false);
     // a tuned choice (0 = two launches, 1 = persistent) overrides the rule
     const bool persist_pays = ctx->tune_choice >= 0 ? ctx->tune_choice == 1
@@ -1015,6 +1018,11 @@ rl_status run_device(rl_ctx *ctx, const void *f, const void *u0, void *u_out, in
         op = OP_RECT;
     else if (path == RL_PATH_STENCIL && ctx->sq_k)
         op = OP_STENCIL;
+    else if (path == RL_PATH_SAT) {
+        if (!ctx->rect) return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate: the SAT path takes uniform rectangles only");
+        if (thin) return fail(ctx, RL_ERR_UNSUPPORTED, "rl_iterate: the SAT path has no selective convolution");
+        op = OP_SAT;
+    }
     if (op >= 0) {
         if (ctx->q_px < plane) {
             sfree(ctx, ctx->qplane);
@@ -1540,7 +1548,7 @@ static rl_status selftest_wait_timeout_impl(int device, int wait_ms) {
         (void)cudaGetLastError();
         return RL_ERR_CUDA;
     }
-    const int W = 128, H = 128, tiles = (W / rl::disc_tile()) * (H / rl::disc_tile());
+    const int W = 128, H = 128, tiles = (W / rl::disc_tile()) * (H / rl::disc_persist_tile_h());
     float *buf = nullptr;  // f, work u, out, q
     int *scratch = nullptr;
     cudaStream_t s = nullptr;
@@ -1570,7 +1578,7 @@ static rl_status selftest_wait_timeout_impl(int device, int wait_ms) {
         p.q_pitch = W;
         p.K = 1;
         p.tiles_x = W / rl::disc_tile();
-        p.tiles_y = H / rl::disc_tile();
+        p.tiles_y = H / rl::disc_persist_tile_h();
         p.progress = scratch;
         p.ticket = (unsigned *)(scratch + tiles);
         p.status = scratch + tiles + 1;

@@ -65,6 +65,11 @@ cudaError_t launch_tile_f16(const IterArgs &a, bool thin, int mode, TileShape ts
 // iteration = two launches sharing the library-owned FP32 q plane.
 constexpr int kDiscMaxRadius = 16;
 constexpr int disc_tile() { return 64; }  // output tile edge of the two-half kernels
+// The persistent disc kernel's tiles are 64 x this (64: the two-half
+// kernels' tile).  A 64 x 32 tile (64 threads) doubles the work items but
+// measured slower at every size (halo staging and prefix passes per output
+// grow by a fifth).
+constexpr int disc_persist_tile_h() { return 64; }
 // Resident CTAs per SM the two-half kernels are compiled for (register cap of
 // their launch bounds; the staged tile fits as many): seven up to R = 8, six
 // up to 12, five beyond, five with selective convolution or R = 1.
@@ -158,6 +163,14 @@ cudaError_t launch_rect(const IterArgs &a, int lox, int hix, int loy, int hiy, i
 cudaError_t launch_rect_r4(const IterArgs &, int, int, int, int, int, bool, float *, long long, cudaStream_t);
 cudaError_t launch_rect_r8(const IterArgs &, int, int, int, int, int, bool, float *, long long, cudaStream_t);
 cudaError_t launch_rect_r16(const IterArgs &, int, int, int, int, int, bool, float *, long long, cudaStream_t);
+
+// Uniform rectangle by a summed-area table in 64-bit fixed point (k_sat.cu):
+// the same tap offsets and halo classes as launch_rect; no thinning.
+cudaError_t launch_sat(const IterArgs &a, int lox, int hix, int loy, int hiy, int storage, float *qplane,
+                       long long q_pitch, cudaStream_t s);
+cudaError_t launch_sat_r4(const IterArgs &, int, int, int, int, int, float *, long long, cudaStream_t);
+cudaError_t launch_sat_r8(const IterArgs &, int, int, int, int, int, float *, long long, cudaStream_t);
+cudaError_t launch_sat_r16(const IterArgs &, int, int, int, int, int, float *, long long, cudaStream_t);
 
 // Exact-transpose band between the two halves (a.fold_ct set): A^T q on the
 // pixels within (fold_rx, fold_ry) of the border, from the full q plane.

@@ -23,12 +23,12 @@ RL_OK, RL_ERR_INVALID_ARG, RL_ERR_UNSUPPORTED, RL_ERR_OOM, RL_ERR_CUDA, \
 RL_PSF_MOTION, RL_PSF_DISC, RL_PSF_DENSE = range(3)
 RL_STORAGE_F32, RL_STORAGE_BF16, RL_STORAGE_F16 = range(3)
 RL_BOUNDARY_MIRROR, RL_BOUNDARY_CLAMP = range(2)
-RL_PATH_AUTO, RL_PATH_RUNSUM, RL_PATH_SPAN, RL_PATH_STENCIL = range(4)
+RL_PATH_AUTO, RL_PATH_RUNSUM, RL_PATH_SPAN, RL_PATH_STENCIL, RL_PATH_SAT = range(5)
 
 STORAGE = {"f32": RL_STORAGE_F32, "bf16": RL_STORAGE_BF16, "f16": RL_STORAGE_F16}
 BOUNDARY = {"mirror": RL_BOUNDARY_MIRROR, "clamp": RL_BOUNDARY_CLAMP}
 PATH = {"auto": RL_PATH_AUTO, "runsum": RL_PATH_RUNSUM, "span": RL_PATH_SPAN,
-        "stencil": RL_PATH_STENCIL}
+        "stencil": RL_PATH_STENCIL, "sat": RL_PATH_SAT}
 PATH_NAME = {v: k for k, v in PATH.items()}
 STATUS_NAME = {RL_OK: "RL_OK", RL_ERR_INVALID_ARG: "RL_ERR_INVALID_ARG",
                RL_ERR_UNSUPPORTED: "RL_ERR_UNSUPPORTED", RL_ERR_OOM: "RL_ERR_OOM",
