@@ -937,48 +937,58 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
             }
         }
     }
+    // Natural block of this thread: a warp covers 8 (x) x 4 (y) blocks -- the
+    // 8 lanes of a 16-byte load phase share a block row -- and the warps tile
+    // the NBX x (GTY / GSY) blocks row group by row group.
+    const int nbx = (lane & 7) + 8 * (wid % (NBX / 8)), nby = wid / (NBX / 8) * 4 + (lane >> 3);
+    // Selective convolution: is any pixel of this thread's block used this
+    // iteration?  The mask loads go out now, while the halo lands.
+    bool blk_any = false;
+    if (THIN && !a.full) {
+        for (int i = 0; i < GSY; ++i) {
+            const int y = y0 + nby * GSY + i, x = x0 + nbx * SX;
+            if (y < a.H && x < a.W) {
+                const uint8_t *mrow = a.mask_in + (long long)y * a.mi_pitch + x;
+                if (x + SX <= a.W && ((reinterpret_cast<uintptr_t>(mrow) & 7) == 0)) {
+                    blk_any |= *reinterpret_cast<const unsigned long long *>(mrow) != 0ull;
+                } else {
+                    for (int j = 0; j < SX && x + j < a.W; ++j) blk_any |= mrow[j] != 0;
+                }
+            }
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
     if constexpr (Op::kPrepass) {
         Op::template prepass<FWD>(sm, sm + G::NR * G::HP, prm);
         __syncthreads();
     }
-    // Natural block of this thread: a warp covers 8 (x) x 4 (y) blocks -- the
-    // 8 lanes of a 16-byte load phase share a block row -- and the warps tile
-    // the NBX x (GTY / GSY) blocks row group by row group.
-    const int nbx = (lane & 7) + 8 * (wid % (NBX / 8)), nby = wid / (NBX / 8) * 4 + (lane >> 3);
     // Selective convolution: compact the blocks with at least one pixel used
     // this iteration (warp ballot + prefix over the warps) and convolve only
     // those; warps left without blocks retire early.
     int n_active = GTX / SX * GTY / GSY;
     __shared__ int blist[GTX / SX * GTY / GSY];
     __shared__ int wcount[4];
+    bool compact = false;  // a block list is used (some block has no used pixel)
     if (THIN && !a.full) {
-        bool any = false;
-        for (int i = 0; i < GSY; ++i) {
-            const int y = y0 + nby * GSY + i, x = x0 + nbx * SX;
-            if (y < a.H && x < a.W) {
-                const uint8_t *mrow = a.mask_in + (long long)y * a.mi_pitch + x;
-                if (x + SX <= a.W && ((reinterpret_cast<uintptr_t>(mrow) & 7) == 0)) {
-                    any |= *reinterpret_cast<const unsigned long long *>(mrow) != 0ull;
-                } else {
-                    for (int j = 0; j < SX && x + j < a.W; ++j) any |= mrow[j] != 0;
-                }
-            }
-        }
+        const bool any = blk_any;
         const unsigned bal = __ballot_sync(0xffffffffu, any);
         if (lane == 0) wcount[wid] = __popc(bal);
         __syncthreads();
         int off = 0;
         for (int k = 0; k < wid; ++k) off += wcount[k];
         n_active = wcount[0] + wcount[1] + wcount[2] + wcount[3];
-        if (any) blist[off + __popc(bal & ((1u << lane) - 1u))] = nby * (GTX / SX) + nbx;
-        __syncthreads();
+        // every block used (the usual case): keep the natural layout
+        compact = n_active < NT;
+        if (compact) {
+            if (any) blist[off + __popc(bal & ((1u << lane) - 1u))] = nby * (GTX / SX) + nbx;
+            __syncthreads();
+        }
     }
 #pragma unroll 1
     for (int e = threadIdx.x; e < n_active; e += NT) {
         int bx = nbx, by = nby;
-        if (THIN && !a.full) {
+        if (THIN && compact) {
             const int b = blist[e];
             bx = b % (GTX / SX);
             by = b / (GTX / SX);
