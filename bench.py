@@ -61,7 +61,7 @@ def kernel_key(name: str) -> str:
     """Short kernel name from ncu's demangled one: template arguments kept,
     namespaces and the parameter list dropped."""
     name = name.split("(")[0].replace("void ", "").strip()
-    return re.sub(r"\brl::(disc::|mtb::)?", "", name)
+    return re.sub(r"(\b\w+|<unnamed>|\(anonymous namespace\))::", "", name)
 
 
 def ingest_ncu(csv_path: str, out_path: str, workload: str, command: str) -> dict:
@@ -627,6 +627,7 @@ def main():
                          "workload (2000 requests at 20 / 50 / 100 / 200 per second), instead of "
                          "the bench line")
     ap.add_argument("--no-config3", action="store_true", help="skip the 4096^2 thinned sub-measurement")
+    ap.add_argument("--no-config1", action="store_true", help="skip the 256^2 sub-measurement")
     ap.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "COMMAND"), default=None,
                     help="write profiles/traffic_plain_2048.json from an ncu CSV (launch list with "
                          "dram__bytes_{read,write}.sum) of COMMAND, tagged with this build's source hash")
@@ -767,7 +768,8 @@ def main():
                     "d2h_bytes_per_step": 3 * plane},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "clocks": clk}
-    line["config1"] = config1_run(local)
+    if not args.no_config1:
+        line["config1"] = config1_run(local)
     if not args.no_batch:
         line["batch"] = batch_run(local)
         line["batch_bf16"] = batch_run(local, storage="bf16")
