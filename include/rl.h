@@ -145,7 +145,8 @@ typedef struct {
                                    sum path could keep whole rows resident
                                    for all iterations, or the disc path run
                                    them all in one persistent launch      */
-#define RL_FLAG_AUTOTUNE 8      /* choose the disc path's launch form, the
+#define RL_FLAG_AUTOTUNE 8      /* choose the disc path's launch form (not
+                                   with RL_FLAG_PERSISTENT), the
                                    running-sum chunk width and the stencil
                                    tile shape by timing the candidates on the
                                    first call for a (site, PSF, size,
@@ -295,7 +296,10 @@ typedef struct {
 typedef struct rl_batch rl_batch;
 
 /* Create a batch of `slots` >= 1 streams on cfg->device (cfg->stream is
- * ignored: the batch creates its own non-blocking streams). */
+ * ignored: the batch creates its own non-blocking streams).  Unless
+ * cfg->flags has RL_FLAG_PER_ITERATION, the slots add RL_FLAG_PERSISTENT:
+ * plain disc solves run as one persistent launch each, which shares the GPU
+ * between streams better than two launches per iteration. */
 rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out);
 /* Queue a job; *ticket identifies it for rl_batch_query / rl_batch_wait. */
 rl_status rl_batch_submit(rl_batch *b, const rl_job *job, long long *ticket);

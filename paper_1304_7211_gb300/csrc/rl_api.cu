@@ -1173,7 +1173,11 @@ TuneSite tune_site(const rl_ctx *ctx, int W, int H, const rl_thinning *thin) {
         snprintf(buf, sizeof buf, "motion-chunk:L%d%s:%dx%d:%s:%s:%s:sm%d", L, ctx->axis ? "y" : "x", W, H, sto,
                  bnd, th, ctx->sms);
     } else if (path == RL_PATH_SPAN && ctx->kind == RL_PSF_DISC && ctx->disc_radius >= 1 &&
-               ctx->disc_radius <= rl::kDiscMaxRadius && !thin && !needs_fold(ctx)) {
+               ctx->disc_radius <= rl::kDiscMaxRadius && !thin && !needs_fold(ctx) &&
+               !(ctx->flags & RL_FLAG_PERSISTENT)) {
+        // (RL_FLAG_PERSISTENT is the caller's decision -- a batch sets it: a
+        // small persistent solve is slower alone, which is what the timing
+        // sees, but shares the GPU with the other streams better)
         t.candidates = {0, 1};
         snprintf(buf, sizeof buf, "disc-form:r%d:%dx%d:%s:%s:%s:sm%d", ctx->disc_radius, W, H, sto, bnd, th,
                  ctx->sms);

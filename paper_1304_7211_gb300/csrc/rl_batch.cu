@@ -231,6 +231,12 @@ rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out) {
             }
             rl_config sc = c;
             sc.stream = s.stream;
+            // Plain disc solves in the persistent form: all iterations in one
+            // launch whose grid is capped at the image's tiles, which shares the
+            // GPU between streams better than two launches per iteration
+            // (bit-identical; measured on the batched workload: 73 against 62-66
+            // Gpx-it/s).  A tuned choice still overrides it.
+            if (!(sc.flags & RL_FLAG_PER_ITERATION)) sc.flags |= RL_FLAG_PERSISTENT;
             rl_status st = rl_create(&sc, &s.ctx);
             if (st != RL_OK) {
                 rl_batch_destroy(b);
