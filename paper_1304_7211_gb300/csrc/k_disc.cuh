@@ -853,12 +853,14 @@ __device__ __forceinline__ void st_seg(T *p, int n, const float (&v)[SX]) {
 
 // Eight bytes of a mask row segment (byte j = pixel j, non-zero = active) as
 // one 8-byte access when whole and aligned, else the first n bytes.
+template <bool COH = false>
 __device__ __forceinline__ unsigned long long ld_mask8(const uint8_t *p, int n) {
-    if (n == SX && (reinterpret_cast<uintptr_t>(p) & 7) == 0) return *reinterpret_cast<const unsigned long long *>(p);
+    if (n == SX && (reinterpret_cast<uintptr_t>(p) & 7) == 0)
+        return gld<COH>(reinterpret_cast<const unsigned long long *>(p));
     unsigned long long v = 0;
 #pragma unroll
     for (int j = 0; j < SX; ++j)
-        if (j < n) v |= (unsigned long long)p[j] << (8 * j);
+        if (j < n) v |= (unsigned long long)gld<COH>(p + j) << (8 * j);
     return v;
 }
 
@@ -898,7 +900,7 @@ constexpr int op_min_blocks() {
 // CTA or per work item.
 template <typename T, bool THIN, typename Op, bool FWD, bool COH = false>
 __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::Params &prm, float *qplane,
-                                          long long q_pitch, int tbx, int tby) {
+                                          long long q_pitch, int tbx, int tby, int full, int update_mask) {
     constexpr int R = Op::kR;
     constexpr int GTX = Op::kTX, GTY = Op::kTY, GSY = Op::kSY;
     constexpr int NBX = GTX / SX;  // block columns of the tile
@@ -915,7 +917,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     // Selective convolution at tile granularity: a tile none of whose pixels
     // is active does nothing (u stays, q keeps the stale ratios).
     int *tflag = (THIN && a.tile_flags) ? a.tile_flags + tby * a.tiles_x + tbx : nullptr;
-    if (tflag && !a.full && *tflag == 0) return;
+    if (tflag && !full && gld<COH>(tflag) == 0) return;
     if (FWD)
         stage_halo<T, G::NR, G::NU, G::HP, COH, NT>(sm, a.clamp, a.W, a.H, y0 - R, x0 - G::R4, (const T *)a.u_in, a.in_pitch,
                                     threadIdx.x);
@@ -944,15 +946,15 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     // Selective convolution: is any pixel of this thread's block used this
     // iteration?  The mask loads go out now, while the halo lands.
     bool blk_any = false;
-    if (THIN && !a.full) {
+    if (THIN && !full) {
         for (int i = 0; i < GSY; ++i) {
             const int y = y0 + nby * GSY + i, x = x0 + nbx * SX;
             if (y < a.H && x < a.W) {
                 const uint8_t *mrow = a.mask_in + (long long)y * a.mi_pitch + x;
                 if (x + SX <= a.W && ((reinterpret_cast<uintptr_t>(mrow) & 7) == 0)) {
-                    blk_any |= *reinterpret_cast<const unsigned long long *>(mrow) != 0ull;
+                    blk_any |= gld<COH>(reinterpret_cast<const unsigned long long *>(mrow)) != 0ull;
                 } else {
-                    for (int j = 0; j < SX && x + j < a.W; ++j) blk_any |= mrow[j] != 0;
+                    for (int j = 0; j < SX && x + j < a.W; ++j) blk_any |= gld<COH>(mrow + j) != 0;
                 }
             }
         }
@@ -970,7 +972,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     __shared__ int blist[GTX / SX * GTY / GSY];
     __shared__ int wcount[4];
     bool compact = false;  // a block list is used (some block has no used pixel)
-    if (THIN && !a.full) {
+    if (THIN && !full) {
         const bool any = blk_any;
         const unsigned bal = __ballot_sync(0xffffffffu, any);
         if (lane == 0) wcount[wid] = __popc(bal);
@@ -1046,7 +1048,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
             if (y >= a.H || n <= 0) break;
             const unsigned long long ones = 0x0101010101010101ull;
             const unsigned long long m =
-                a.full ? ones : ld_mask8(a.mask_in + (long long)y * a.mi_pitch + xb, n);
+                full ? ones : ld_mask8<COH>(a.mask_in + (long long)y * a.mi_pitch + xb, n);
             if (FWD) {
                 if (m == 0) continue;  // no pixel of the segment used: q keeps its stale ratios
                 float e[SX], o[SX];
@@ -1080,7 +1082,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
                 }
                 st_seg<T>((T *)a.u_out + (long long)y * a.out_pitch + xb, n, o);
                 if (n < SX) mo &= (1ull << (8 * n)) - 1ull;  // bytes past the row end
-                if (a.update_mask && !a.replay) {
+                if (update_mask && !a.replay) {
                     st_mask8(a.mask_out + (long long)y * a.m_pitch + xb, n, mo);
                     tile_any |= mo != 0;
                 }
@@ -1089,7 +1091,7 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     }
     if (!FWD && THIN) {
         if (a.active_count) warp_count_add(a.active_count, used);
-        if (tflag && a.update_mask) {
+        if (tflag && update_mask) {
             // does any pixel of the tile stay active for the next iteration?
             // (blocks not processed had no active pixel and keep mask 0)
             const int cnt = __syncthreads_count(tile_any);
@@ -1108,7 +1110,7 @@ __global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, THIN>())
     // every CTA of this one has started.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" :::);
-    half_tile<T, THIN, Op, FWD>(a, prm, qplane, q_pitch, blockIdx.x, blockIdx.y);
+    half_tile<T, THIN, Op, FWD>(a, prm, qplane, q_pitch, blockIdx.x, blockIdx.y, a.full, a.update_mask);
 }
 
 // Batched (request, tile) form: CTA b runs tile items[b].y of job items[b].x,
@@ -1125,7 +1127,7 @@ __global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
     const TileJob &job = jobs[it.x];
     const IterArgs &a = job.a[phase];
     const int tiles_x = (a.W + Op::kTX - 1) / Op::kTX;
-    half_tile<float, false, Op, FWD>(a, prm, job.qplane, job.q_pitch, it.y % tiles_x, it.y / tiles_x);
+    half_tile<float, false, Op, FWD>(a, prm, job.qplane, job.q_pitch, it.y % tiles_x, it.y / tiles_x, 1, 0);
 }
 
 // ---- persistent form --------------------------------------------------------
@@ -1160,8 +1162,8 @@ __device__ __forceinline__ bool wait_tile(const int *w, int need, int *status, u
     }
 }
 
-template <typename T, typename Op>
-__global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
+template <typename T, typename Op, bool THIN>
+__global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, THIN>())
     k_disc_persist(const __grid_constant__ PersistArgs p, const __grid_constant__ typename Op::Params prm) {
     __shared__ int s_item;
     const int n_tiles = p.tiles_x * p.tiles_y;
@@ -1185,10 +1187,14 @@ __global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
         if (!__syncthreads_and(ok)) break;
         const int k = hk >> 1;
         const IterArgs &a = p.a[(k > 0) + 2 * (k == p.K - 1)];
+        // selective convolution: every pixel used when k % P == 0; the mask
+        // is rewritten every iteration (Q = 1) or on those only (Q = P)
+        const int full = !THIN || k % p.thin_p == 0;
+        const int update_mask = THIN && (p.thin_q == 1 || full);
         if ((hk & 1) == 0)
-            half_tile<T, false, Op, true, true>(a, prm, p.qplane, p.q_pitch, tbx, tby);
+            half_tile<T, THIN, Op, true, true>(a, prm, p.qplane, p.q_pitch, tbx, tby, full, update_mask);
         else
-            half_tile<T, false, Op, false, true>(a, prm, p.qplane, p.q_pitch, tbx, tby);
+            half_tile<T, THIN, Op, false, true>(a, prm, p.qplane, p.q_pitch, tbx, tby, full, update_mask);
         // every store of the tile is issued; publish them, then the progress
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1198,18 +1204,18 @@ __global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
     }
 }
 
-template <typename Op, typename T>
+template <typename Op, typename T, bool THIN>
 cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cudaStream_t s) {
     constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
     // tiles of this op (the host sized progress for 64 x 64 tiles, at least as many)
     p.tiles_x = (p.a[0].W + Op::kTX - 1) / Op::kTX;
     p.tiles_y = (p.a[0].H + Op::kTY - 1) / Op::kTY;
-    cudaError_t e = ensure_smem<k_disc_persist<T, Op>>(smem);
+    cudaError_t e = ensure_smem<k_disc_persist<T, Op, THIN>>(smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disc_persist<T, Op>, Op::kNT, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_disc_persist<T, Op, THIN>, Op::kNT, smem)) !=
         cudaSuccess)
         return e;
     if (occ < 1) return cudaErrorNotSupported;
@@ -1227,15 +1233,17 @@ cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cuda
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_disc_persist<T, Op>, p, prm);
+    return cudaLaunchKernelEx(&cfg, k_disc_persist<T, Op, THIN>, p, prm);
 }
 
 template <typename Op>
 cudaError_t launch_persist(const PersistArgs &p, const typename Op::Params &prm, int storage, cudaStream_t s) {
+    const bool thin = p.thin_p > 0;
     switch (storage) {
-    case ST_F32: return launch_persist_t<Op, float>(p, prm, s);
-    case ST_BF16: return launch_persist_t<Op, __nv_bfloat16>(p, prm, s);
-    case ST_F16: return launch_persist_t<Op, __half>(p, prm, s);
+    case ST_F32: return thin ? launch_persist_t<Op, float, true>(p, prm, s) : launch_persist_t<Op, float, false>(p, prm, s);
+    case ST_BF16: return thin ? launch_persist_t<Op, __nv_bfloat16, true>(p, prm, s)
+                              : launch_persist_t<Op, __nv_bfloat16, false>(p, prm, s);
+    case ST_F16: return thin ? launch_persist_t<Op, __half, true>(p, prm, s) : launch_persist_t<Op, __half, false>(p, prm, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -882,7 +882,7 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
     // a tuned choice (0 = two launches, 1 = persistent) overrides the rule
     const bool persist_pays = ctx->tune_choice >= 0 ? ctx->tune_choice == 1
                                                     : 4LL * tx * ty >= 5LL * slots;  // at least 1.25 tiles per slot
-    if (op == OP_DISC && !thin && !a.fold_ct && !(ctx->flags & RL_FLAG_PER_ITERATION) &&
+    if (op == OP_DISC && !sched && !a.fold_ct && !(ctx->flags & RL_FLAG_PER_ITERATION) &&
         (persist_pays || ((ctx->flags & RL_FLAG_PERSISTENT) && ctx->tune_choice < 0))) {
         const size_t n = (size_t)tx * ty + 2;  // progress per tile, ticket, status
         rl_status st = grow(ctx, (void **)&ctx->pscratch, &ctx->pscratch_bytes, n * sizeof(int),
@@ -904,10 +904,23 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         pa.ticket = (unsigned *)(ctx->pscratch + tx * ty);
         pa.status = ctx->pscratch + tx * ty + 1;
         pa.wait_ns = 2000000000ull;  // 2 s for one neighbour tile: only a fault gets near it
+        if (thin) {  // the mask and the u plane are updated in place; u_out is written after
+            pa.thin_p = thin->reset_period;
+            pa.thin_q = thin->update_period;
+        }
         const cudaError_t e = rl::launch_disc_persist(pa, ctx->storage, R, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: persistent launch");
         ctx->pstatus = pa.status;
         ctx->launches += 1;
+        if (thin) {
+            CK(cudaMemcpy2DAsync(u_out, pitch * es, work, sp * es, W * es, H, cudaMemcpyDeviceToDevice,
+                                 ctx->stream),
+               "rl_iterate: copy out");
+            ctx->last_mask = ctx->mask[0];
+            ctx->last_W = W;
+            ctx->last_H = H;
+            ctx->last_mp = sp;
+        }
         return RL_OK;
     }
     // iteration 0 reads the start image; the middle iterations repeat with

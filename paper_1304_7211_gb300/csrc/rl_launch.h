@@ -117,7 +117,9 @@ RL_DECLARE_TILES_R(13) RL_DECLARE_TILES_R(14) RL_DECLARE_TILES_R(15) RL_DECLARE_
 // the first reads the start image, the last writes the caller's buffer, the
 // others work in place on a library u plane.  progress, ticket and status
 // are zeroed before the launch; a wait longer than wait_ns sets status to 1
-// and every CTA returns.  No thinning, no transpose band.
+// and every CTA returns.  Selective convolution (thin_p > 0) on the default
+// tile with its tile flags and an in-place mask; no replayed schedules, no
+// transpose band.
 struct PersistArgs {
     IterArgs a[4];
     float *qplane;
@@ -128,6 +130,7 @@ struct PersistArgs {
     unsigned *ticket;          // next work item
     int *status;               // 0, or 1 when a wait gave up
     unsigned long long wait_ns;
+    int thin_p, thin_q;        // selective convolution: reset and mask-update periods (0 = none)
 };
 // Launch with a grid of every co-resident CTA (occupancy x SMs); returns
 // cudaErrorNotSupported when the radius has no persistent kernel.

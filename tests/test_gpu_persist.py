@@ -86,3 +86,37 @@ def test_bounded_wait_gives_up_and_reports():
     a, _ = run(spec, f, 5, "f32", "mirror", per_iteration=False)
     b, _ = run(spec, f, 5, "f32", "mirror", per_iteration=True)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("thin", [(1e-3, True, 10, 10), (1e-3, True, 10, 1), (0.05, False, 10, 1)],
+                         ids=["rel-q10", "rel-q1", "abs-q1"])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_thinned_persistent_equals_two_launch_form(thin, storage):
+    """Selective convolution (Eq. 4-5) in the persistent kernel: the mask,
+    the tile flags and the stale ratios are updated in place as in the two
+    launches per iteration, so images, final masks and active counts agree
+    exactly."""
+    from paper_1304_7211_gb300 import rl
+    spec = synth.disc(6)
+    W, H, K = 333, 250, 27
+    c = synth.make_case(W, H, spec, 0, "poisson", synth.SEED_BASE + 152)
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[storage]
+    f = torch.from_numpy(c.f.astype(np.float32)).cuda().to(dt)
+    outs = []
+    for flags in (rl.RL_FLAG_PERSISTENT, rl.RL_FLAG_PER_ITERATION):
+        ctx = rl.rl_create(0, None, storage, "mirror", "auto", flags)
+        try:
+            rl.rl_set_psf(ctx, spec)
+            u = torch.empty_like(f)
+            st = rl.rl_iterate(ctx, f, None, u, W, H, W, K, rl.thinning(*thin), stats=True)
+            m = np.zeros((H, W), np.uint8)
+            rl.rl_get_mask(ctx, m, W)
+        finally:
+            rl.rl_destroy(ctx)
+        torch.cuda.synchronize()
+        outs.append((u, m, st))
+    (ua, ma, sa), (ub, mb, sb) = outs
+    assert sa.launches == 1
+    assert torch.equal(ua, ub)
+    np.testing.assert_array_equal(ma, mb)
+    assert sa.active_pixel_iterations == sb.active_pixel_iterations < W * H * K
