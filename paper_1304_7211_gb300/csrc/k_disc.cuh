@@ -267,12 +267,14 @@ __device__ __forceinline__ void f2add(unsigned long long &acc, unsigned long lon
 }
 
 // Disc geometry: spare units at the end of every staged row hold the row
-// prefix's last entry (at unit hunit(NU), which is NU or NU + 1).  Three of
-// them make the row pitch an odd number of units, so the prefix pass (one
-// thread per row, all at the same unit) puts 8 consecutive rows on 8
-// distinct bank quads.
+// prefix's last entry (at unit hunit(NU), which is NU or NU + 1): one spare
+// unit, or three when hunit(NU) = NU + 1, so that the row pitch is an odd
+// number of units and the prefix pass (one thread per row, all at the same
+// unit) puts 8 consecutive rows on 8 distinct bank quads.  (Eight CTAs per
+// SM, which the smaller pitch would allow up to R = 8 at a 64-register cap,
+// measured slower.)
 template <int R, int TXg = TX, int TYg = TY>
-using DiscHalo = Halo<R, 3, TXg, TYg>;
+using DiscHalo = Halo<R, ((((TXg + 2 * round4(R)) / 4) >> 3) & 1) ? 3 : 1, TXg, TYg>;
 
 // Exclusive prefix of every staged row, in place: logical column k of a row
 // (0 <= k <= 4 NU, the last in the spare unit) becomes the sum of columns
