@@ -85,3 +85,22 @@ def test_sat_refuses_other_psfs_and_thinning():
             d.run(f, 3, thin=rl.thinning(1e-3))
         assert e.value.status == rl.RL_ERR_UNSUPPORTED
         d.run(f, 3)  # the context goes on
+
+
+def test_sat_bf16_storage():
+    """BF16 storage on the table path: f and u rounded to BF16, the table
+    built from the staged FP32 values; within K unit roundoffs of the oracle
+    on the rounded f (the rectangle's amplification is small at 7 x 5)."""
+    spec = synth.dense(np.ones((7, 5)))
+    c = synth.make_case(190, 150, spec, 0, "poisson", synth.SEED_BASE + 192)
+    f_r = torch.from_numpy(c.f.astype(np.float32)).to(torch.bfloat16)
+    from paper_1304_7211_gb300 import rl
+    with rl.Deconvolver(spec, path="sat", storage="bf16") as d:
+        u = d.run(f_r.cuda(), 10)
+    torch.cuda.synchronize()
+    with rl.Deconvolver(spec, path="span", storage="bf16") as d:
+        v = d.run(f_r.cuda(), 10)
+    torch.cuda.synchronize()
+    ref = oracle.rl(f_r.float().numpy().astype(np.float64), oracle.psf_dense(np.ones((7, 5)), 2, 3), 10).u
+    assert oracle.rel_linf(u.float().cpu().numpy(), ref) <= 10 * 2.0 ** -9
+    assert oracle.rel_linf(u.float().cpu().numpy(), v.float().cpu().numpy().astype(np.float64)) <= 10 * 2.0 ** -9
