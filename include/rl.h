@@ -326,11 +326,15 @@ const char *rl_batch_last_error(const rl_batch *b);
 /*
  * Batched (request, tile) form of the disc and box kernels (Eq. 3 per job;
  * Sec. 3 defocus disc and rectangular box blur): n jobs that share ctx's PSF
- * run as one forward and one adjoint launch per iteration over the 64 x 64
- * tiles of every job still iterating, so many small images fill the GPU
- * that one image alone would leave mostly idle.  A job leaves the work list
- * when its own iteration count ends; each job's result is, bit for bit, the
- * image that rl_iterate on ctx gives for it alone.
+ * run over the 64 x 64 tiles of every job still iterating, so many small
+ * images fill the GPU that one image alone would leave mostly idle.  When
+ * the jobs have at least 1.25 tiles per resident CTA (or ctx has
+ * RL_FLAG_PERSISTENT), every iteration of every job runs in one persistent
+ * cooperative launch, each tile waiting only for the tiles around it in its
+ * own job; otherwise (and always with RL_FLAG_PER_ITERATION) as one forward
+ * and one adjoint launch per iteration.  A job leaves the work list when its own iteration count ends;
+ * each job's result is, bit for bit, the image that rl_iterate on ctx gives
+ * for it alone.
  *   ctx: its PSF must take the disc or box kernel (RL_PSF_DISC of radius
  *       1..16, or dense taps forming a uniform centred odd square up to
  *       33 x 33); path AUTO or SPAN; FP32 storage; no exact-transpose band
@@ -339,10 +343,13 @@ const char *rl_batch_last_error(const rl_batch *b);
  *       until the work is done; u_out may alias u0 but not f; W, H, pitch
  *       (elements), iterations.  psf is ignored (ctx's PSF applies); thin,
  *       f_host and u_host must be NULL.
- * Enqueued on ctx's stream (as rl_iterate); the library's scratch, one u and
- * one q plane per job, is allocated and released in stream order.
+ * Enqueued on ctx's stream (as rl_iterate); the persistent form then waits
+ * for the stream, to read the kernel's status word before its scratch is
+ * released.  The library's scratch, one u and one q plane per job, is
+ * allocated and released in stream order.
  * Errors: RL_ERR_INVALID_ARG, RL_ERR_STATE (no PSF), RL_ERR_UNSUPPORTED (PSF,
- * storage, band, thinning or host buffers), RL_ERR_CUDA, RL_ERR_OOM.
+ * storage, band, thinning or host buffers), RL_ERR_TIMEOUT (a bounded wait of
+ * the persistent form gave up), RL_ERR_CUDA, RL_ERR_OOM.
  */
 rl_status rl_iterate_tiles(rl_ctx *ctx, const rl_job *jobs, int n);
 

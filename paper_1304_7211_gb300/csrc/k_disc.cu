@@ -47,6 +47,19 @@ cudaError_t launch_tiles(int op, int radius, const TileJob *jobs, const int2 *it
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_tiles_persist(int op, int radius, const TilesPersistArgs &p, cudaStream_t s) {
+    switch (radius) {
+#define RL_TP_CASE(R)                                                                       \
+    case R:                                                                                 \
+        return op == 0 ? launch_disc_tiles_persist_r##R(p, s) : launch_box_tiles_persist_r##R(p, s);
+    RL_TP_CASE(1) RL_TP_CASE(2) RL_TP_CASE(3) RL_TP_CASE(4) RL_TP_CASE(5) RL_TP_CASE(6) RL_TP_CASE(7)
+    RL_TP_CASE(8) RL_TP_CASE(9) RL_TP_CASE(10) RL_TP_CASE(11) RL_TP_CASE(12) RL_TP_CASE(13) RL_TP_CASE(14)
+    RL_TP_CASE(15) RL_TP_CASE(16)
+#undef RL_TP_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_disc_persist(const PersistArgs &p, int storage, int radius, cudaStream_t s) {
     switch (radius) {
 #define RL_PERSIST_CASE(R) \

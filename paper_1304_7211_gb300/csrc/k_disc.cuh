@@ -1206,6 +1206,76 @@ __global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, THIN>())
     }
 }
 
+// Batched persistent form: the half-step of a ticket by binary search over
+// the half-steps' first tickets, then the same wait / tile body / publish as
+// the one-image kernel, with the job's arguments from the table.
+template <typename Op>
+__global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
+    k_tiles_persist(const __grid_constant__ TilesPersistArgs p, const __grid_constant__ typename Op::Params prm) {
+    __shared__ int s_item;
+    const int total = p.start[p.n_halves];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.ticket, 1u);
+        __syncthreads();
+        const int tk = s_item;
+        if (tk >= total) break;
+        int lo = 0, hi = p.n_halves - 1;  // last half-step whose start <= tk
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.start[mid] <= tk) lo = mid;
+            else hi = mid - 1;
+        }
+        const int hk = lo, idx = tk - p.start[hk];
+        const int2 it = p.items[idx];
+        const TileJob &job = p.jobs[it.x];
+        const IterArgs &a = job.a[hk >= 2 ? 1 : 0];
+        const int tx = p.tiles_x[it.x], ty = (a.H + Op::kTY - 1) / Op::kTY;
+        const int tbx = it.y % tx, tby = it.y / tx;
+        bool ok = true;
+        if (hk > 0 && threadIdx.x < 9) {
+            const int nx = tbx + (int)threadIdx.x % 3 - 1, ny = tby + (int)threadIdx.x / 3 - 1;
+            if (nx >= 0 && nx < tx && ny >= 0 && ny < ty)
+                ok = wait_tile(p.progress + p.first[it.x] + ny * tx + nx, hk, p.status, p.wait_ns);
+        }
+        if (!__syncthreads_and(ok)) break;
+        if ((hk & 1) == 0)
+            half_tile<float, false, Op, true, true>(a, prm, job.qplane, job.q_pitch, tbx, tby, 1, 0);
+        else
+            half_tile<float, false, Op, false, true>(a, prm, job.qplane, job.q_pitch, tbx, tby, 1, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(p.progress + idx, hk + 1);
+        }
+    }
+}
+
+template <typename Op>
+cudaError_t launch_tiles_persist_t(const TilesPersistArgs &p, const typename Op::Params &prm, cudaStream_t s) {
+    constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
+    cudaError_t e = ensure_smem<k_tiles_persist<Op>>(smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles_persist<Op>, Op::kNT, smem)) != cudaSuccess)
+        return e;
+    if (occ < 1) return cudaErrorNotSupported;
+    const long long grid = std::min<long long>((long long)occ * sms, (long long)p.n_items0);
+    if (grid < 1) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(Op::kNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tiles_persist<Op>, p, prm);
+}
+
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cudaStream_t s) {
     constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
@@ -1331,6 +1401,9 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
                                        int phase, cudaStream_t s) {                          \
         return disc::launch_op_tiles<disc::DiscOp<R>>(jobs, items, n_items, phase, {}, s);   \
     }                                                                                        \
+    cudaError_t launch_disc_tiles_persist_r##R(const TilesPersistArgs &p, cudaStream_t s) {  \
+        return disc::launch_tiles_persist_t<disc::DiscOp<R>>(p, {}, s);                      \
+    }                                                                                        \
     cudaError_t launch_disc_persist_r##R(const PersistArgs &p, int storage, cudaStream_t s) { \
         return disc::launch_persist<disc::DiscOp<R>>(p, {}, storage, s);                     \
     }                                                                                        \
@@ -1345,6 +1418,9 @@ cudaError_t launch_op(const IterArgs &a, const typename Op::Params &prm, int sto
     cudaError_t launch_box_tiles_r##R(const TileJob *jobs, const int2 *items, int n_items,   \
                                       int phase, cudaStream_t s) {                           \
         return disc::launch_op_tiles<disc::BoxOp<R>>(jobs, items, n_items, phase, {}, s);    \
+    }                                                                                        \
+    cudaError_t launch_box_tiles_persist_r##R(const TilesPersistArgs &p, cudaStream_t s) {   \
+        return disc::launch_tiles_persist_t<disc::BoxOp<R>>(p, {}, s);                       \
     }                                                                                        \
     }
 

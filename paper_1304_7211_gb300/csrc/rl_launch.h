@@ -98,9 +98,35 @@ struct TileJob {
 // op 0 = disc, 1 = box; radius 1..16
 cudaError_t launch_tiles(int op, int radius, const TileJob *jobs, const int2 *items, int n_items, int phase,
                          cudaStream_t s);
+
+// Persistent form of the batched (request, tile) launches: every iteration
+// of every job in one cooperative launch.  The items of half-step hk (hk = 2k:
+// forward of iteration k, 2k + 1: adjoint) are the first count[hk] entries of
+// `items` (jobs sorted by iteration count, descending); half-step hk's
+// tickets start at start[hk] (start[2 kmax] = total).  An item waits for the
+// tiles around it in its own job (`first[j]`: index of job j's first item,
+// `tiles_x[j]` its tile columns) to finish half-step hk - 1.  progress (one
+// per item of half-step 0), ticket and status are zeroed before the launch.
+struct TilesPersistArgs {
+    const TileJob *jobs;
+    const int2 *items;
+    const int *start;          // 2 kmax + 1 ticket offsets
+    const int *count;          // items per half-step
+    const int *first;          // per job: index of its first item
+    const int *tiles_x;        // per job: tile columns
+    int n_halves;              // 2 kmax
+    int n_items0;              // items of half-step 0
+    int *progress;
+    unsigned *ticket;
+    int *status;
+    unsigned long long wait_ns;
+};
+cudaError_t launch_tiles_persist(int op, int radius, const TilesPersistArgs &p, cudaStream_t s);
 #define RL_DECLARE_TILES_R(R)                                                                 \
     cudaError_t launch_disc_tiles_r##R(const TileJob *, const int2 *, int, int, cudaStream_t); \
-    cudaError_t launch_box_tiles_r##R(const TileJob *, const int2 *, int, int, cudaStream_t);
+    cudaError_t launch_box_tiles_r##R(const TileJob *, const int2 *, int, int, cudaStream_t);  \
+    cudaError_t launch_disc_tiles_persist_r##R(const TilesPersistArgs &, cudaStream_t);        \
+    cudaError_t launch_box_tiles_persist_r##R(const TilesPersistArgs &, cudaStream_t);
 RL_DECLARE_TILES_R(1) RL_DECLARE_TILES_R(2) RL_DECLARE_TILES_R(3) RL_DECLARE_TILES_R(4)
 RL_DECLARE_TILES_R(5) RL_DECLARE_TILES_R(6) RL_DECLARE_TILES_R(7) RL_DECLARE_TILES_R(8)
 RL_DECLARE_TILES_R(9) RL_DECLARE_TILES_R(10) RL_DECLARE_TILES_R(11) RL_DECLARE_TILES_R(12)

@@ -126,3 +126,27 @@ def test_tiles_errors():
             rl.rl_iterate_tiles(d.ctx, [(f, None, u, 4, 80, 80, 3)])
         assert e.value.status == rl.RL_ERR_INVALID_ARG
         rl.rl_iterate_tiles(d.ctx, [])  # no jobs: nothing to do
+
+
+@pytest.mark.parametrize("spec", [synth.disc(8), synth.dense(np.ones((9, 9)))], ids=lambda s: s.name)
+def test_persistent_tiles_equal_launch_per_iteration(spec):
+    """The batched form's one persistent launch (every iteration of every job)
+    against its launch pair per iteration (RL_FLAG_PER_ITERATION): same tile
+    arithmetic, so the same bits, for a mix of 24 sizes and iteration counts."""
+    from paper_1304_7211_gb300 import rl
+    rng = np.random.default_rng(synth.SEED_BASE + 83)
+    jobs = []
+    for j in range(24):
+        W, H = int(rng.integers(40, 400)), int(rng.integers(40, 400))
+        K = int(rng.integers(0, 45))
+        c = synth.make_case(W, H, spec, 0, "poisson", synth.SEED_BASE + 300 + j)
+        jobs.append((torch.from_numpy(c.f.astype(np.float32)).cuda(), W, H, K))
+    outs = []
+    for flags in (rl.RL_FLAG_PERSISTENT, rl.RL_FLAG_PER_ITERATION):
+        us = [torch.full_like(f, -1.0) for f, *_ in jobs]
+        with rl.Deconvolver(spec, flags=flags) as d:
+            rl.rl_iterate_tiles(d.ctx, [(f, None, u, W, H, W, K) for (f, W, H, K), u in zip(jobs, us)])
+        torch.cuda.synchronize()
+        outs.append(us)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
