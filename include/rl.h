@@ -327,12 +327,10 @@ const char *rl_batch_last_error(const rl_batch *b);
  * Batched (request, tile) form of the disc and box kernels (Eq. 3 per job;
  * Sec. 3 defocus disc and rectangular box blur): n jobs that share ctx's PSF
  * run over the 64 x 64 tiles of every job still iterating, so many small
- * images fill the GPU that one image alone would leave mostly idle.  When
- * the jobs have at least 1.25 tiles per resident CTA (or ctx has
- * RL_FLAG_PERSISTENT), every iteration of every job runs in one persistent
- * cooperative launch, each tile waiting only for the tiles around it in its
- * own job; otherwise (and always with RL_FLAG_PER_ITERATION) as one forward
- * and one adjoint launch per iteration.  A job leaves the work list when its own iteration count ends;
+ * images fill the GPU that one image alone would leave mostly idle: one
+ * forward and one adjoint launch per iteration, or, with RL_FLAG_PERSISTENT
+ * on ctx, every iteration of every job in one persistent cooperative launch
+ * in which each tile waits only for the tiles around it in its own job.  A job leaves the work list when its own iteration count ends;
  * each job's result is, bit for bit, the image that rl_iterate on ctx gives
  * for it alone.
  *   ctx: its PSF must take the disc or box kernel (RL_PSF_DISC of radius

@@ -1209,7 +1209,8 @@ TuneSite tune_site(const rl_ctx *ctx, int W, int H, const rl_thinning *thin) {
 // the call's own inputs (a warm-up run, then the faster of two timed runs of
 // up to 10 iterations, into library scratch; CUDA events on the context
 // stream) and caches the fastest; later calls with the key take the cached
-// choice.  In a batch the timing shares the GPU with the other streams.
+// choice.  The device is drained first, so that in a batch the other
+// streams' work does not decide the choice.
 rl_status tune_if_needed(rl_ctx *ctx, const void *f, const void *u0, int W, int H, long long pitch, int K,
                          const rl_thinning *thin) {
     ctx->tune_choice = -1;
@@ -1227,6 +1228,9 @@ rl_status tune_if_needed(rl_ctx *ctx, const void *f, const void *u0, int W, int 
     const int kt = K < 10 ? K : 10;
     float best_ms = 0.f;
     std::string times;
+    // time the candidates on a quiet GPU: in a batch the other streams'
+    // work would otherwise decide the choice (a one-time stall per key)
+    CK(cudaDeviceSynchronize(), "rl_iterate: tuning");
     for (int c : site.candidates) {
         ctx->tune_choice = c;
         int path = 0;
@@ -1477,13 +1481,13 @@ static rl_status iterate_tiles_impl(rl_ctx *ctx, const rl_job *jobs, int n) {
     // the persistent form's tables: half-step starts and counts, per-job first
     // item and tile columns, per-item progress, ticket and status
     const int kmax = jobs[ord[0]].iterations;
-    // as for one image: the persistent form pays from about 1.25 tiles per
-    // resident CTA slot (measured: 64 frames of 128^2..512^2 under a disc r8,
-    // about 330 tiles, 46.6 Gpx-it/s persistent against 50.6 with a launch
-    // pair per iteration), or when RL_FLAG_PERSISTENT asks for it
-    const long long tslots = (long long)ctx->sms * rl::disc_min_blocks(R, false);
+    // The persistent form only when RL_FLAG_PERSISTENT asks for it: each job's
+    // tiles form a small grid whose per-tile chain of items sets the pace
+    // (measured: 64 frames of 128^2..512^2 under a disc r8, about 1300
+    // tiles, 46.6 Gpx-it/s persistent against 50.6 with a launch pair per
+    // iteration).
     const bool persistent = !(ctx->flags & RL_FLAG_PER_ITERATION) && kmax > 0 &&
-                            ((ctx->flags & RL_FLAG_PERSISTENT) || 4LL * (long long)items.size() >= 5LL * tslots);
+                            (ctx->flags & RL_FLAG_PERSISTENT);
     std::vector<int> tstart, tcount, tfirst(n), ttx(n);
     if (persistent) {
         int active = n, acc = 0;
