@@ -947,18 +947,19 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
     const int nbx = (lane & 7) + 8 * (wid % (NBX / 8)), nby = wid / (NBX / 8) * 4 + (lane >> 3);
     // Selective convolution: is any pixel of this thread's block used this
     // iteration?  The mask loads go out now, while the halo lands.
+    // The mask words are kept in shared memory (4 KB after the staged tile
+    // and the op's extra floats) for the epilogue of this block: in
+    // registers they would spill across the block sums.
     bool blk_any = false;
+    unsigned long long *bmask = reinterpret_cast<unsigned long long *>(sm + G::NR * G::HP + Op::kExtraFloats);
     if (THIN && !full) {
+#pragma unroll
         for (int i = 0; i < GSY; ++i) {
             const int y = y0 + nby * GSY + i, x = x0 + nbx * SX;
-            if (y < a.H && x < a.W) {
-                const uint8_t *mrow = a.mask_in + (long long)y * a.mi_pitch + x;
-                if (x + SX <= a.W && ((reinterpret_cast<uintptr_t>(mrow) & 7) == 0)) {
-                    blk_any |= gld<COH>(reinterpret_cast<const unsigned long long *>(mrow)) != 0ull;
-                } else {
-                    for (int j = 0; j < SX && x + j < a.W; ++j) blk_any |= gld<COH>(mrow + j) != 0;
-                }
-            }
+            unsigned long long mw = 0ull;
+            if (y < a.H && x < a.W) mw = ld_mask8<COH>(a.mask_in + (long long)y * a.mi_pitch + x, min(SX, a.W - x));
+            bmask[i * NT + threadIdx.x] = mw;
+            blk_any |= mw != 0ull;
         }
     }
     cp_async_wait_all();
@@ -1042,29 +1043,39 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
             continue;
         }
         // selective convolution (Eq. 4-5), one row segment of SX pixels at a
-        // time: mask bytes as one 8-byte access, f / u and u' as 16-byte ones
+        // time: mask bytes as one 8-byte access, f / u and u' as 16-byte ones.
+        // The segment's mask is cut to its n pixels first, so every pixel
+        // step below is branch-free (selects and predicated stores); the
+        // arguments it needs are read once, into registers.
         const int n = min(SX, a.W - xb);
+        const float w = a.weight, tau = a.tau;
+        const bool rel = a.relative != 0;
+        const bool write_mask = update_mask && !a.replay;
+        const long long mip = a.mi_pitch;
+        const uint8_t *mrow = full ? nullptr : a.mask_in + (long long)yb * mip + xb;
+        const unsigned long long ones = 0x0101010101010101ull;
+        const unsigned long long valid = n >= SX ? ~0ull : (n > 0 ? (1ull << (8 * n)) - 1ull : 0ull);
 #pragma unroll
         for (int i = 0; i < GSY; ++i) {
             const int y = yb + i;
             if (y >= a.H || n <= 0) break;
-            const unsigned long long ones = 0x0101010101010101ull;
+            // the block's own mask words were loaded with the halo, unless the
+            // block list gave this thread another block
             const unsigned long long m =
-                full ? ones : ld_mask8<COH>(a.mask_in + (long long)y * a.mi_pitch + xb, n);
+                (full ? ones : (compact ? ld_mask8<COH>(mrow + i * mip, n) : bmask[i * NT + threadIdx.x])) & valid;
             if (FWD) {
                 if (m == 0) continue;  // no pixel of the segment used: q keeps its stale ratios
                 float e[SX], o[SX];
                 ld_seg<T>((const T *)a.f + (long long)y * a.f_pitch + xb, n, e);
 #pragma unroll
-                for (int j = 0; j < SX; ++j)
-                    o[j] = rl_ratio(e[j], Op::kUniform ? acc[i][j] * a.weight : acc[i][j]);
+                for (int j = 0; j < SX; ++j) o[j] = rl_ratio(e[j], Op::kUniform ? acc[i][j] * w : acc[i][j]);
                 float *qrow = qplane + (long long)y * q_pitch + xb;
-                if (m == ones) {
-                    st_seg<float>(qrow, n, o);
+                if (m == ones) {  // every pixel used (then n == SX)
+                    st_seg<float>(qrow, SX, o);
                 } else {
 #pragma unroll
                     for (int j = 0; j < SX; ++j)
-                        if (j < n && ((m >> (8 * j)) & 0xff)) qrow[j] = o[j];
+                        if ((m >> (8 * j)) & 0xff) qrow[j] = o[j];
                 }
             } else {
                 float uv[SX], o[SX];
@@ -1073,18 +1084,16 @@ __device__ __forceinline__ void half_tile(const IterArgs &a, const typename Op::
 #pragma unroll
                 for (int j = 0; j < SX; ++j) {
                     const float u = uv[j];
-                    const float c = Op::kUniform ? acc[i][j] * a.weight : acc[i][j];
+                    const float c = Op::kUniform ? acc[i][j] * w : acc[i][j];
                     const bool use = ((m >> (8 * j)) & 0xff) != 0;
                     const float un = use ? u * c : u;
                     o[j] = un;
-                    if (j < n) used += use;
-                    float d = 0.f;
-                    if (use) d = a.relative ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
-                    mo |= (unsigned long long)(use && d >= a.tau) << (8 * j);
+                    used += use;
+                    const float d = rel ? (u > 0.f ? fabsf(c - 1.f) : 0.f) : fabsf(un - u);
+                    mo |= (unsigned long long)(use && d >= tau) << (8 * j);
                 }
                 st_seg<T>((T *)a.u_out + (long long)y * a.out_pitch + xb, n, o);
-                if (n < SX) mo &= (1ull << (8 * n)) - 1ull;  // bytes past the row end
-                if (update_mask && !a.replay) {
+                if (write_mask) {
                     st_mask8(a.mask_out + (long long)y * a.m_pitch + xb, n, mo);
                     tile_any |= mo != 0;
                 }
@@ -1130,6 +1139,14 @@ __global__ void __launch_bounds__(Op::kNT, op_min_blocks<Op, false>())
     const IterArgs &a = job.a[phase];
     const int tiles_x = (a.W + Op::kTX - 1) / Op::kTX;
     half_tile<float, false, Op, FWD>(a, prm, job.qplane, job.q_pitch, it.y % tiles_x, it.y / tiles_x, 1, 0);
+}
+
+// Dynamic shared memory of the tile body: the staged tile, the op's extra
+// floats and, with selective convolution, one 8-byte mask word per block row.
+template <typename Op, bool THIN>
+constexpr size_t tile_smem() {
+    return Op::Geom::bytes + Op::kExtraFloats * sizeof(float) +
+           (THIN ? (size_t)Op::kSY * Op::kNT * sizeof(unsigned long long) : 0);
 }
 
 // ---- persistent form --------------------------------------------------------
@@ -1278,7 +1295,7 @@ cudaError_t launch_tiles_persist_t(const TilesPersistArgs &p, const typename Op:
 
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cudaStream_t s) {
-    constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
+    constexpr size_t smem = tile_smem<Op, THIN>();
     // tiles of this op (the host sized progress for 64 x 64 tiles, at least as many)
     p.tiles_x = (p.a[0].W + Op::kTX - 1) / Op::kTX;
     p.tiles_y = (p.a[0].H + Op::kTY - 1) / Op::kTY;
@@ -1323,7 +1340,7 @@ cudaError_t launch_persist(const PersistArgs &p, const typename Op::Params &prm,
 template <typename Op, typename T, bool THIN>
 cudaError_t launch_one(const IterArgs &a, const typename Op::Params &prm, float *qplane,
                        long long q_pitch, cudaStream_t s) {
-    constexpr size_t smem = Op::Geom::bytes + Op::kExtraFloats * sizeof(float);
+    constexpr size_t smem = tile_smem<Op, THIN>();
     cudaError_t e = ensure_smem<k_disc_half<T, THIN, Op, true>>(smem);
     if (e == cudaSuccess) e = ensure_smem<k_disc_half<T, THIN, Op, false>>(smem);
     if (e != cudaSuccess) return e;
