@@ -60,8 +60,9 @@ def source_sha() -> str:
 def kernel_key(name: str) -> str:
     """Short kernel name from ncu's demangled one: template arguments kept,
     namespaces and the parameter list dropped."""
-    name = name.split("(")[0].replace("void ", "").strip()
-    return re.sub(r"(\b\w+|<unnamed>|\(anonymous namespace\))::", "", name)
+    name = name.replace("(anonymous namespace)::", "").split("(")[0].replace("void ", "").strip()
+    # ncu prints the anonymous namespace as "<unnamed>::" or "unnamed>::"
+    return re.sub(r"(<?unnamed>|\(anonymous namespace\)|\b\w+)::", "", name)
 
 
 def ingest_ncu(csv_path: str, out_path: str, workload: str, command: str) -> dict:
