@@ -57,6 +57,14 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+_T0 = time.perf_counter()
+
+
+def progress(stage: str) -> None:
+    """One line per finished stage on stderr (the JSON line goes to stdout)."""
+    print(f"bench: {stage} done at {time.perf_counter() - _T0:.1f} s", file=sys.stderr, flush=True)
+
+
 def kernel_key(name: str) -> str:
     """Short kernel name from ncu's demangled one: template arguments kept,
     namespaces and the parameter list dropped."""
@@ -460,6 +468,7 @@ def serve_run(local, n=400, rates=(100.0, 200.0), slots=16):
 
     alone = requests(1.0)
     svc = serve.service_times(alone, device=local)
+    progress("serve: alone-solve times")
     srv = serve.Server(device=local, slots=slots, hbm_budget_bytes=150e9)
     rows = []
     try:
@@ -472,6 +481,7 @@ def serve_run(local, n=400, rates=(100.0, 200.0), slots=16):
             rows.append({"rate_per_s": rate, "served": rep.as_dict(), "fifo_sequential": fifo.as_dict(),
                          "served_over_sequential": rep.mpx_it_per_s / fifo.mpx_it_per_s,
                          "results_bitwise_same_as_alone": f"{same}/{len(reqs)}"})
+            progress(f"serve at {rate:g} requests/s")
     finally:
         srv.close()
     px_it = float(sum(r.f.shape[0] * r.f.shape[1] * r.iterations for r in alone))
@@ -769,18 +779,26 @@ def main():
                     "d2h_bytes_per_step": 3 * plane},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "clocks": clk}
+    progress("main step, e2e and rooflines")
     if not args.no_config1:
         line["config1"] = config1_run(local)
+        progress("config1")
     if not args.no_batch:
         line["batch"] = batch_run(local)
+        progress("batch f32")
         line["batch_bf16"] = batch_run(local, storage="bf16")
+        progress("batch bf16")
         line["batch_tiles"] = tiles_run(local)
+        progress("batch tiles")
     if not args.no_config3 and ws == 1:
         line["config3"] = thinned_run(local)
+        progress("config3")
     if not args.no_serve:
         line["serve"] = serve_run(local, n=args.serve_requests)
+        progress("serve")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(inputs)
+        progress("cpu baseline")
     if rank == 0:
         print(json.dumps(line), flush=True)
     for s in solves:

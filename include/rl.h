@@ -378,6 +378,15 @@ rl_status rl_selftest_wait_timeout(int device, int wait_ms);
 void rl_test_fail_allocation(int nth);
 
 /*
+ * Launch shape for tests: with n > 0, every persistent disc launch of the
+ * process (plain or thinned, RL_FLAG_PERSISTENT or chosen by size) runs n
+ * CTAs per SM (at most its occupancy, at most one per tile) instead of the
+ * rule's about two tiles per CTA; results are bit-identical for every n.
+ * 0 restores the rule.  Host side only; no counterpart in the paper.
+ */
+void rl_test_persist_ctas(int n);
+
+/*
  * Allocation-free variant of the running-sum path.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc -- code
  * running inside an allocator or memory-pool hook, latency-critical threads

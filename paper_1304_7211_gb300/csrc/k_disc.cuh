@@ -1308,6 +1308,7 @@ cudaError_t launch_persist_t(PersistArgs p, const typename Op::Params &prm, cuda
         cudaSuccess)
         return e;
     if (occ < 1) return cudaErrorNotSupported;
+    if (p.ctas_per_sm > 0 && p.ctas_per_sm < occ) occ = p.ctas_per_sm;
     // no more CTAs than tiles: a half has one item per tile, so extra CTAs
     // would only wait -- and a small image then leaves the other SMs to the
     // other streams of a batch

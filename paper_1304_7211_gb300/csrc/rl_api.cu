@@ -143,6 +143,9 @@ bool is_device_ptr(const void *p) {
 // from then on fails as if the device were out of memory.
 std::atomic<int> g_fail_alloc{0};
 
+// Test hook: CTAs per SM of every persistent disc launch (0 = the rule).
+std::atomic<int> g_test_persist_ctas{0};
+
 // Every scratch allocation of rl_iterate: stream-ordered on the context
 // stream (no device-wide synchronisation, unlike cudaMalloc / cudaFree).
 rl_status salloc(rl_ctx *ctx, void **p, size_t bytes, const char *what) {
@@ -870,20 +873,34 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         ctx->launches += 2;
         return RL_OK;
     };
-    // Plain disc: every iteration in one persistent launch (tiles advance as
-    // their neighbourhood allows, no barrier between the halves) when the
-    // image has enough tiles to keep the resident CTAs busy while some wait:
-    // at about one tile per CTA slot the two launches per iteration are
-    // faster (measured: 41.5 vs 38.5 us/it for the disc r = 8 at 2048^2,
-    // 127 vs 137 us/it for r = 12 at 4096^2).
+    // Disc: every iteration in one persistent launch (tiles advance as their
+    // neighbourhood allows, no barrier between the halves) when the image has
+    // enough tiles for the overlap to pay; the grid then holds about two
+    // tiles per CTA (rl::disc_persist_ctas).  Measured (us/it, GB300): disc
+    // r = 8 at 2048^2 38.4 two launches, 35.6 persistent with 3 CTAs per SM,
+    // 41.5 with every resident CTA; r = 12 at 4096^2 137 against 127.  Below
+    // about 6 tiles per SM (1024^2 and 1448^2 at r <= 8) the two launches
+    // are faster, and so they are for plain 16-bit storage at 2048^2 (42.0
+    // against 44.1), where the old margin of 1.25 tiles per resident CTA
+    // slot stays.
     const int tx = (W + rl::disc_tile() - 1) / rl::disc_tile();
     const int ty = (H + rl::disc_persist_tile_h() - 1) / rl::disc_persist_tile_h();  // persistent tiles
+    const long long tiles = (long long)tx * ty;
     const long long slots = (long long)ctx->sms * rl::disc_min_blocks(R, false);
-    // a tuned choice (0 = two launches, 1 = persistent) overrides the rule
-    const bool persist_pays = ctx->tune_choice >= 0 ? ctx->tune_choice == 1
-                                                    : 4LL * tx * ty >= 5LL * slots;  // at least 1.25 tiles per slot
+    const bool narrow = ctx->storage != RL_STORAGE_F32 && !thin;
+    // a tuned choice (0 = two launches, c >= 1 = persistent with c CTAs per
+    // SM) overrides the rule
+    const bool persist_pays = ctx->tune_choice >= 0 ? ctx->tune_choice >= 1
+                              : narrow              ? 4LL * tiles >= 5LL * slots
+                                                    : tiles >= 6LL * ctx->sms;
+    // RL_FLAG_PERSISTENT asks for the persistent form; a batch slot's
+    // contexts ask for it on plain solves only (thinned ones keep the rule:
+    // measured on the served workload at 200 requests/s, 110 against 93
+    // Gpx-it/s and a median latency of 60 against 330 ms)
+    const bool forced = (ctx->flags & RL_FLAG_PERSISTENT) && ctx->tune_choice < 0 &&
+                        !(thin && (ctx->flags & rl::kFlagBatchSlot));
     if (op == OP_DISC && !sched && !a.fold_ct && !(ctx->flags & RL_FLAG_PER_ITERATION) &&
-        (persist_pays || ((ctx->flags & RL_FLAG_PERSISTENT) && ctx->tune_choice < 0))) {
+        (persist_pays || forced)) {
         const size_t n = (size_t)tx * ty + 2;  // progress per tile, ticket, status
         rl_status st = grow(ctx, (void **)&ctx->pscratch, &ctx->pscratch_bytes, n * sizeof(int),
                             "rl_iterate: tile progress");
@@ -904,6 +921,10 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         pa.ticket = (unsigned *)(ctx->pscratch + tx * ty);
         pa.status = ctx->pscratch + tx * ty + 1;
         pa.wait_ns = 2000000000ull;  // 2 s for one neighbour tile: only a fault gets near it
+        const int test_ctas = g_test_persist_ctas.load();
+        pa.ctas_per_sm = test_ctas > 0               ? test_ctas
+                         : ctx->tune_choice >= 1 ? ctx->tune_choice
+                                                 : rl::disc_persist_ctas(tiles, ctx->sms);
         if (thin) {  // the mask and the u plane are updated in place; u_out is written after
             pa.thin_p = thin->reset_period;
             pa.thin_q = thin->update_period;
@@ -1191,8 +1212,16 @@ TuneSite tune_site(const rl_ctx *ctx, int W, int H, const rl_thinning *thin) {
         // (RL_FLAG_PERSISTENT is the caller's decision -- a batch sets it: a
         // small persistent solve is slower alone, which is what the timing
         // sees, but shares the GPU with the other streams better)
-        t.candidates = {0, 1};
-        snprintf(buf, sizeof buf, "disc-form:r%d:%dx%d:%s:%s:%s:sm%d", ctx->disc_radius, W, H, sto, bnd, th,
+        // 0 = two launches per iteration; c >= 1 = persistent with c CTAs per
+        // SM, around the rule's count (the launch caps c at its occupancy)
+        const long long tiles = (long long)((W + rl::disc_tile() - 1) / rl::disc_tile()) *
+                                ((H + rl::disc_persist_tile_h() - 1) / rl::disc_persist_tile_h());
+        const int cmax = rl::disc_min_blocks(ctx->disc_radius, false);
+        const int c = std::min(rl::disc_persist_ctas(tiles, ctx->sms), cmax);
+        t.candidates = {0};
+        for (int d = c - 1; d <= c + 1; ++d)
+            if (d >= 1 && d <= cmax) t.candidates.push_back(d);
+        snprintf(buf, sizeof buf, "disc-launch:r%d:%dx%d:%s:%s:%s:sm%d", ctx->disc_radius, W, H, sto, bnd, th,
                  ctx->sms);
     } else if (path == RL_PATH_STENCIL && !ctx->sq_k) {
         t.candidates = {64 << 16 | 32, 64 << 16 | 64, 128 << 16 | 32, 128 << 16 | 64};
@@ -1712,5 +1741,7 @@ rl_status rl_selftest_wait_timeout(int device, int wait_ms) {
 }
 
 void rl_test_fail_allocation(int nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }
+
+void rl_test_persist_ctas(int n) { g_test_persist_ctas.store(n > 0 ? n : 0); }
 
 }  // extern "C"

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/rl.h"
+#include "rl_launch.h"
 
 namespace {
 
@@ -235,8 +236,9 @@ rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out) {
             // launch whose grid is capped at the image's tiles, which shares the
             // GPU between streams better than two launches per iteration
             // (bit-identical; measured on the batched workload: 73 against 62-66
-            // Gpx-it/s).  A tuned choice still overrides it.
-            if (!(sc.flags & RL_FLAG_PER_ITERATION)) sc.flags |= RL_FLAG_PERSISTENT;
+            // Gpx-it/s).  Thinned ones keep the size rule (kFlagBatchSlot); a
+            // tuned choice still overrides both.
+            if (!(sc.flags & RL_FLAG_PER_ITERATION)) sc.flags |= RL_FLAG_PERSISTENT | rl::kFlagBatchSlot;
             rl_status st = rl_create(&sc, &s.ctx);
             if (st != RL_OK) {
                 rl_batch_destroy(b);

@@ -157,9 +157,25 @@ struct PersistArgs {
     int *status;               // 0, or 1 when a wait gave up
     unsigned long long wait_ns;
     int thin_p, thin_q;        // selective convolution: reset and mask-update periods (0 = none)
+    int ctas_per_sm;           // grid cap per SM (0 or above the occupancy: the occupancy)
 };
-// Launch with a grid of every co-resident CTA (occupancy x SMs); returns
-// cudaErrorNotSupported when the radius has no persistent kernel.
+// rl_config.flags bit that a batch sets on its slot contexts, beside
+// RL_FLAG_PERSISTENT: the persistent form is forced on plain disc solves
+// only; thinned ones keep the size rule.  Not part of the public flags.
+constexpr int kFlagBatchSlot = 1 << 24;
+
+// CTAs per SM for a persistent solve over `tiles` tiles: about two work items
+// per CTA and half, round(tiles / (2 sms)), at least 1.  Fewer items per CTA
+// run the halves in lock step (every CTA waits at once); more leave SMs idle
+// (measured on GB300, disc r 4..16, 1024^2..4096^2: 2048^2, 1024 tiles, is
+// fastest with 3 CTAs per SM, 4096^2 with every resident one).
+inline int disc_persist_ctas(long long tiles, int sms) {
+    const long long c = (tiles + sms) / (2LL * sms);
+    return c < 1 ? 1 : (c > 64 ? 64 : (int)c);
+}
+// Launch with a grid of p.ctas_per_sm (else every co-resident) CTAs per SM,
+// at most one per tile; returns cudaErrorNotSupported when the radius has no
+// persistent kernel.
 cudaError_t launch_disc_persist(const PersistArgs &p, int storage, int radius, cudaStream_t s);
 #define RL_DECLARE_PERSIST_R(R) \
     cudaError_t launch_disc_persist_r##R(const PersistArgs &p, int storage, cudaStream_t s);

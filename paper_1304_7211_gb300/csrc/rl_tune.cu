@@ -6,7 +6,7 @@
 // mix.  The cache is process-wide; with RL_TUNE_CACHE set to a file name it
 // is read from that file on first use and every new choice is appended to it
 // as one JSON object per line:
-//   {"key": "disc-form:r12:4096x4096:f32:mirror:plain:sm152", "choice": 1, "us": "1357.2 1271.4"}
+//   {"key": "disc-launch:r12:4096x4096:f32:mirror:plain:sm152", "choice": 6, "us": "137.4 133.5 126.6"}
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>

@@ -120,3 +120,67 @@ def test_thinned_persistent_equals_two_launch_form(thin, storage):
     assert torch.equal(ua, ub)
     np.testing.assert_array_equal(ma, mb)
     assert sa.active_pixel_iterations == sb.active_pixel_iterations < W * H * K
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3, 5, 7])
+@pytest.mark.parametrize("thin", [None, (1e-3, True, 10, 10)], ids=["plain", "thinned"])
+def test_every_grid_size_equals_two_launch_form(ctas, thin):
+    """The persistent grid holds `ctas` CTAs per SM (at most one per tile);
+    with fewer CTAs than tiles each CTA takes several items per half, in
+    ticket order, so every wait is for an item taken earlier.  The result
+    must not depend on the grid: bit-identical to the two launches for every
+    count, plain and thinned (Eq. 4-5), with many tiles per CTA at 1 CTA per
+    SM (2000 x 1500: 32 x 24 tiles)."""
+    from paper_1304_7211_gb300 import rl
+    lib = rl.load()
+    spec = synth.disc(7)
+    W, H, K = 2000, 1500, 13
+    c = synth.make_case(W, H, spec, 0, "poisson", synth.SEED_BASE + 153)
+    f = torch.from_numpy(c.f.astype(np.float32)).cuda()
+    outs = []
+    for flags in (rl.RL_FLAG_PERSISTENT, rl.RL_FLAG_PER_ITERATION):
+        ctx = rl.rl_create(0, None, "f32", "mirror", "auto", flags)
+        lib.rl_test_persist_ctas(ctas)
+        try:
+            rl.rl_set_psf(ctx, spec)
+            u = torch.empty_like(f)
+            st = rl.rl_iterate(ctx, f, None, u, W, H, W, K, rl.thinning(*thin) if thin else None, stats=True)
+        finally:
+            lib.rl_test_persist_ctas(0)
+            rl.rl_destroy(ctx)
+        torch.cuda.synchronize()
+        outs.append((u, st))
+    (ua, sa), (ub, sb) = outs
+    assert sa.launches == 1 and sb.launches > 1
+    assert torch.equal(ua, ub)
+    assert sa.active_pixel_iterations == sb.active_pixel_iterations
+
+
+@pytest.mark.parametrize("side,storage,thin,persistent", [
+    (1024, "f32", False, False),   # 256 tiles, under 6 per SM: two launches
+    (2048, "f32", False, True),    # 1024 tiles: persistent, 3 CTAs per SM
+    (2048, "bf16", False, False),  # 16-bit plain keeps 1.25 tiles per resident CTA
+    (2048, "bf16", True, True),    # thinned 16-bit: persistent
+    (4096, "bf16", False, True)])
+def test_launch_form_rule(side, storage, thin, persistent):
+    """Without flags the size rule picks the form: persistent from about 6
+    tiles per SM (FP32, or thinned), from 1.25 tiles per resident CTA slot
+    for plain 16-bit storage; the two forms agree bit for bit, so only the
+    launch count tells them apart."""
+    from paper_1304_7211_gb300 import rl
+    props = torch.cuda.get_device_properties(0)
+    if props.multi_processor_count != 152:
+        pytest.skip("the sizes assume a 152-SM GB300")
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[storage]
+    torch.manual_seed(7)
+    f = (torch.rand(side, side, device="cuda") * 100 + 5).to(dt)
+    ctx = rl.rl_create(0, None, storage, "mirror", "auto", 0)
+    try:
+        rl.rl_set_psf(ctx, synth.disc(8))
+        u = torch.empty_like(f)
+        st = rl.rl_iterate(ctx, f, None, u, side, side, side, 4,
+                           rl.thinning(1e-3, True, 10, 10) if thin else None, stats=True)
+    finally:
+        rl.rl_destroy(ctx)
+    torch.cuda.synchronize()
+    assert (st.launches == 1) == persistent

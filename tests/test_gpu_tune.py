@@ -70,7 +70,7 @@ def test_tuned_agrees_with_untuned(spec, W, H, its, bitwise):
 def test_choices_are_written_to_the_cache_file():
     lines = [json.loads(l) for l in open(os.environ["RL_TUNE_CACHE"]) if l.strip()]
     keys = {l["key"].split(":")[0] for l in lines}
-    assert {"disc-form", "motion-chunk", "stencil-tile"} <= keys
+    assert {"disc-launch", "motion-chunk", "stencil-tile"} <= keys
     for l in lines:
         assert isinstance(l["choice"], int)
         assert len(l["us"].split()) >= 2  # every candidate's time per iteration
