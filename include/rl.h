@@ -158,8 +158,9 @@ typedef struct {
                                    choice depends on the request alone    */
 #define RL_FLAG_PERSISTENT 4    /* disc path: one persistent launch for all
                                    iterations even where the image has too
-                                   few tiles for it to pay (about one tile
-                                   per resident CTA); tests and tuning    */
+                                   few tiles for it to pay (under about 6
+                                   per SM), plain or thinned; tests and
+                                   tuning                                 */
 /* The adjoint convolution of Eq. 3.  Default: h* (x) q with the same
  * boundary continuation as the forward one -- h reflected about the origin
  * (Sec. 2), the "pad-flip" operator B.  With this flag: the exact matrix
@@ -277,7 +278,9 @@ const char *rl_last_error(const rl_ctx *ctx);
  *       pointer inside must stay valid until the job is done).
  * Errors: as rl_set_psf / rl_iterate, returned by rl_batch_submit when the
  * job is issued inside that call, else by rl_batch_query / rl_batch_wait of
- * its ticket; RL_ERR_INVALID_ARG for a bad ticket.  No C++ exception crosses
+ * its ticket; RL_ERR_TIMEOUT there when the job's persistent launch gave up
+ * a bounded wait (its image is then incomplete; the other jobs are not
+ * affected); RL_ERR_INVALID_ARG for a bad ticket.  No C++ exception crosses
  * the ABI: host allocation failures come back as RL_ERR_OOM.
  */
 typedef struct {
@@ -297,9 +300,11 @@ typedef struct rl_batch rl_batch;
 
 /* Create a batch of `slots` >= 1 streams on cfg->device (cfg->stream is
  * ignored: the batch creates its own non-blocking streams).  Unless
- * cfg->flags has RL_FLAG_PER_ITERATION, the slots add RL_FLAG_PERSISTENT:
- * plain disc solves run as one persistent launch each, which shares the GPU
- * between streams better than two launches per iteration. */
+ * cfg->flags has RL_FLAG_PER_ITERATION, plain disc solves run as one
+ * persistent launch each, which shares the GPU between streams better than
+ * two launches per iteration; thinned ones take the form the image size
+ * picks (a small thinned solve in one launch would hold its SMs for the
+ * whole solve). */
 rl_status rl_batch_create(const rl_config *cfg, int slots, rl_batch **out);
 /* Queue a job; *ticket identifies it for rl_batch_query / rl_batch_wait. */
 rl_status rl_batch_submit(rl_batch *b, const rl_job *job, long long *ticket);
@@ -385,6 +390,18 @@ void rl_test_fail_allocation(int nth);
  * 0 restores the rule.  Host side only; no counterpart in the paper.
  */
 void rl_test_persist_ctas(int n);
+
+/*
+ * Failure detection for tests (no GPU fault): with ns > 0, every persistent
+ * disc launch of the process gives up a wait for a neighbouring tile after
+ * ns nanoseconds instead of 2 s -- with a few ns and about one tile per
+ * CTA (rl_test_persist_ctas), where each half starts while the previous
+ * one still finishes, a launch over many tiles almost surely gives up.  The launch then records it and returns; the solve
+ * reports RL_ERR_TIMEOUT (rl_iterate on its next synchronising call, a
+ * batch job through rl_batch_query / rl_batch_wait) and its image is
+ * incomplete.  0 restores the bound.  No counterpart in the paper.
+ */
+void rl_test_persist_wait_ns(unsigned long long ns);
 
 /*
  * Allocation-free variant of the running-sum path.  The paper has no

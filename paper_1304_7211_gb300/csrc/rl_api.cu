@@ -85,6 +85,7 @@ struct rl_ctx {
     int *pscratch = nullptr;
     size_t pscratch_bytes = 0;
     const int *pstatus = nullptr;  // status word of the last persistent launch, or NULL
+    int *status_sink = nullptr;    // pinned host word each persistent launch's status is copied to
     // autotuner: the choice in effect for the current call at its tunable
     // site (-1 = the built-in rule), and its scratch output
     int tune_choice = -1;
@@ -143,8 +144,10 @@ bool is_device_ptr(const void *p) {
 // from then on fails as if the device were out of memory.
 std::atomic<int> g_fail_alloc{0};
 
-// Test hook: CTAs per SM of every persistent disc launch (0 = the rule).
+// Test hooks: CTAs per SM of every persistent disc launch (0 = the rule),
+// and the bound of its neighbour waits in ns (0 = 2 s).
 std::atomic<int> g_test_persist_ctas{0};
+std::atomic<unsigned long long> g_test_wait_ns{0};
 
 // Every scratch allocation of rl_iterate: stream-ordered on the context
 // stream (no device-wide synchronisation, unlike cudaMalloc / cudaFree).
@@ -920,7 +923,8 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         pa.progress = ctx->pscratch;
         pa.ticket = (unsigned *)(ctx->pscratch + tx * ty);
         pa.status = ctx->pscratch + tx * ty + 1;
-        pa.wait_ns = 2000000000ull;  // 2 s for one neighbour tile: only a fault gets near it
+        const unsigned long long test_wait = g_test_wait_ns.load();
+        pa.wait_ns = test_wait > 0 ? test_wait : 2000000000ull;  // 2 s for one neighbour tile: only a fault gets near it
         const int test_ctas = g_test_persist_ctas.load();
         pa.ctas_per_sm = test_ctas > 0               ? test_ctas
                          : ctx->tune_choice >= 1 ? ctx->tune_choice
@@ -932,6 +936,9 @@ rl_status run_disc(rl_ctx *ctx, const void *f, const void *start, void *u_out, i
         const cudaError_t e = rl::launch_disc_persist(pa, ctx->storage, R, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rl_iterate: persistent launch");
         ctx->pstatus = pa.status;
+        if (ctx->status_sink)  // in stream order, so it holds this launch's outcome once the stream passes it
+            CK(cudaMemcpyAsync(ctx->status_sink, pa.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+               "rl_iterate: status");
         ctx->launches += 1;
         if (thin) {
             CK(cudaMemcpy2DAsync(u_out, pitch * es, work, sp * es, W * es, H, cudaMemcpyDeviceToDevice,
@@ -1293,6 +1300,12 @@ rl_status tune_if_needed(rl_ctx *ctx, const void *f, const void *u0, int W, int 
 }
 
 }  // namespace
+
+namespace rl {
+void set_status_sink(rl_ctx *ctx, int *host_word) {
+    if (ctx) ctx->status_sink = host_word;
+}
+}  // namespace rl
 
 static rl_status iterate_impl(rl_ctx *ctx, const void *f, const void *u0, void *u_out, int W, int H,
                               long long pitch, int iterations, const rl_thinning *thin, rl_stats *stats) {
@@ -1743,5 +1756,7 @@ rl_status rl_selftest_wait_timeout(int device, int wait_ms) {
 void rl_test_fail_allocation(int nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }
 
 void rl_test_persist_ctas(int n) { g_test_persist_ctas.store(n > 0 ? n : 0); }
+
+void rl_test_persist_wait_ns(unsigned long long ns) { g_test_wait_ns.store(ns); }
 
 }  // extern "C"

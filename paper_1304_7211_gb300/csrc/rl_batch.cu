@@ -19,6 +19,7 @@
 namespace {
 
 constexpr int kDepth = 2;  // jobs in flight per slot
+constexpr int kWordChunk = 64;  // pinned status words allocated at a time
 
 struct Job {
     long long ticket;
@@ -33,6 +34,7 @@ struct Pending {
     long long ticket;
     cudaEvent_t done;
     long long work;
+    int *status;  // pinned word: the job's persistent launch gave up waiting when nonzero
 };
 
 struct Slot {
@@ -57,6 +59,8 @@ struct rl_batch {
     std::vector<Slot> slots;
     std::deque<Job> waiting;  // submitted, not issued
     std::vector<cudaEvent_t> free_events;
+    std::vector<int *> word_chunks;  // pinned host memory, kWordChunk ints each
+    std::vector<int *> free_words;
     std::map<long long, Outcome> outcomes;
     long long next_ticket = 1;
     std::string err;
@@ -69,12 +73,21 @@ rl_status bfail(rl_batch *b, rl_status st, const std::string &m) {
     return st;
 }
 
-// Retire finished jobs at the front of each slot's queue.
+// Retire finished jobs at the front of each slot's queue; a job whose
+// persistent launch gave up waiting (a fault elsewhere on the GPU, not a
+// normal outcome) is recorded as failed with RL_ERR_TIMEOUT.
 void reap(rl_batch *b) {
     for (auto &s : b->slots) {
         while (!s.queue.empty() && cudaEventQuery(s.queue.front().done) == cudaSuccess) {
-            s.queued_work -= s.queue.front().work;
-            b->free_events.push_back(s.queue.front().done);
+            Pending &p = s.queue.front();
+            if (*(volatile int *)p.status != 0 && !b->outcomes.count(p.ticket))
+                b->outcomes[p.ticket] = {RL_ERR_TIMEOUT,
+                                         "rl_batch: the job's persistent launch gave up waiting for "
+                                         "neighbouring tiles; its image is incomplete",
+                                         false};
+            s.queued_work -= p.work;
+            b->free_events.push_back(p.done);
+            b->free_words.push_back(p.status);
             s.queue.pop_front();
         }
         (void)cudaGetLastError();
@@ -92,6 +105,23 @@ bool is_waiting(const rl_batch *b, long long ticket) {
     for (const auto &j : b->waiting)
         if (j.ticket == ticket) return true;
     return false;
+}
+
+// A pinned status word for one job, or NULL when pinned memory ran out.
+int *take_word(rl_batch *b) {
+    if (b->free_words.empty()) {
+        void *chunk = nullptr;
+        if (cudaHostAlloc(&chunk, kWordChunk * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        b->word_chunks.push_back((int *)chunk);
+        for (int i = 0; i < kWordChunk; ++i) b->free_words.push_back((int *)chunk + i);
+    }
+    int *w = b->free_words.back();
+    b->free_words.pop_back();
+    *(volatile int *)w = 0;
+    return w;
 }
 
 // Enqueue one job on slot s: PSF, optional upload, the solve, optional
@@ -115,8 +145,17 @@ rl_status issue(rl_batch *b, Slot &s, Job &j, std::string *msg) {
             return RL_ERR_CUDA;
         }
     }
+    // the persistent launch's status lands here; a word whose job failed
+    // after this point is not reused (a copy into it may still be queued)
+    int *word = take_word(b);
+    if (!word) {
+        *msg = "rl_batch: pinned status word";
+        return RL_ERR_OOM;
+    }
+    rl::set_status_sink(s.ctx, word);
     st = rl_iterate(s.ctx, job.f, job.u0, job.u_out, job.W, job.H, job.pitch, job.iterations,
                     j.has_thin ? &j.thin : nullptr, nullptr);
+    rl::set_status_sink(s.ctx, nullptr);
     if (st != RL_OK) {
         *msg = rl_last_error(s.ctx);
         return st;
@@ -140,7 +179,7 @@ rl_status issue(rl_batch *b, Slot &s, Job &j, std::string *msg) {
         return RL_ERR_CUDA;
     }
     cudaEventRecord(ev, s.stream);
-    s.queue.push_back({j.ticket, ev, j.work});
+    s.queue.push_back({j.ticket, ev, j.work, word});
     s.queued_work += j.work;
     return RL_OK;
 }
@@ -309,6 +348,11 @@ rl_status rl_batch_query(rl_batch *b, long long ticket, int *done) {
         }
         (void)cudaGetLastError();
         *done = e == cudaSuccess;
+        if (*done) {  // reap it, so that a launch that gave up is reported
+            reap(b);
+            auto f = b->outcomes.find(ticket);
+            if (f != b->outcomes.end() && !f->second.cancelled) return bfail(b, f->second.status, f->second.message);
+        }
         return RL_OK;
     });
 }
@@ -333,8 +377,7 @@ rl_status rl_batch_wait(rl_batch *b, long long ticket) {
             if (!p) return RL_OK;  // finished and reaped
             const cudaError_t e = cudaEventSynchronize(p->done);
             if (e != cudaSuccess) return bfail(b, RL_ERR_CUDA, std::string("rl_batch_wait: ") + cudaGetErrorString(e));
-            reap(b);
-            return RL_OK;
+            reap(b);  // records a launch that gave up; the loop reports it
         }
     });
 }
@@ -401,6 +444,7 @@ rl_status rl_batch_destroy(rl_batch *b) {
                 if (s.stream) cudaStreamDestroy(s.stream);
             }
             for (auto ev : b->free_events) cudaEventDestroy(ev);
+            for (auto w : b->word_chunks) cudaFreeHost(w);
         }
         delete b;
         return RL_OK;

@@ -8,6 +8,8 @@
 
 #include "rl_common.cuh"
 
+struct rl_ctx;  // include/rl.h
+
 namespace rl {
 
 enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
@@ -163,6 +165,11 @@ struct PersistArgs {
 // RL_FLAG_PERSISTENT: the persistent form is forced on plain disc solves
 // only; thinned ones keep the size rule.  Not part of the public flags.
 constexpr int kFlagBatchSlot = 1 << 24;
+// Every later persistent launch of ctx copies its status word (0, or 1 when
+// a wait gave up) into *host_word (pinned host memory) on the context's
+// stream after the launch; NULL stops it.  Lets a batch report the outcome
+// of each job without a synchronising call.
+void set_status_sink(rl_ctx *ctx, int *host_word);
 
 // CTAs per SM for a persistent solve over `tiles` tiles: about two work items
 // per CTA and half, round(tiles / (2 sms)), at least 1.  Fewer items per CTA

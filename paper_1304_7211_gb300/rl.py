@@ -90,7 +90,7 @@ EXPORTS = ("rl_create", "rl_set_psf", "rl_iterate", "rl_destroy", "rl_last_error
            "rl_get_mask", "rl_motion_x_noalloc", "rl_batch_create", "rl_batch_submit",
            "rl_batch_query", "rl_batch_wait", "rl_batch_sync", "rl_batch_destroy",
            "rl_batch_last_error", "rl_batch_cancel", "rl_iterate_tiles", "rl_selftest_wait_timeout",
-           "rl_test_fail_allocation", "rl_test_persist_ctas")
+           "rl_test_fail_allocation", "rl_test_persist_ctas", "rl_test_persist_wait_ns")
 RL_NOALLOC_MAX_PIXELS = 4194304
 
 
@@ -139,6 +139,8 @@ def load() -> ctypes.CDLL:
     lib.rl_test_fail_allocation.argtypes = [ctypes.c_int]
     lib.rl_test_persist_ctas.restype = None
     lib.rl_test_persist_ctas.argtypes = [ctypes.c_int]
+    lib.rl_test_persist_wait_ns.restype = None
+    lib.rl_test_persist_wait_ns.argtypes = [ctypes.c_ulonglong]
     lib.rl_iterate_tiles.restype = ctypes.c_int
     lib.rl_iterate_tiles.argtypes = [P, ctypes.POINTER(rl_job), ctypes.c_int]
     lib.rl_motion_x_noalloc.restype = ctypes.c_int

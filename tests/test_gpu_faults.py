@@ -4,7 +4,8 @@ An allocation failure forced through the library's test hook must come back
 as RL_ERR_OOM with a message, leave the context usable, and -- in a batch --
 fail only the job it hit: the jobs before and after it give the same images
 as alone.  A job cancelled before it starts never runs; one already on the
-GPU runs to the end and is reported cancelled.
+GPU runs to the end and is reported cancelled.  A persistent launch that
+gives up a bounded wait is reported for its own job.
 """
 import numpy as np
 import pytest
@@ -119,3 +120,39 @@ def test_cancel_before_start_and_while_running(lib):
     torch.cuda.synchronize()
     assert bool((u_c == -1.0).all())  # never ran
     assert torch.equal(u_b, alone(spec, f_big, 300))
+
+
+def test_persistent_give_up_is_reported_per_batch_job(lib):
+    """A neighbour wait that runs out in a batch job's persistent launch (the
+    wait bound shortened to 1 ns through the test hook; with one tile per CTA
+    every CTA that finishes a half takes an item of the next one while its
+    neighbours still compute, so items do wait; nothing faults, the launch
+    records it and returns) fails that job alone with RL_ERR_TIMEOUT; the
+    other job is exact, and with the bound restored the same job matches its
+    alone-solve bit for bit."""
+    from paper_1304_7211_gb300 import rl
+    spec, other = synth.disc(7), synth.motion(9, 0)
+    f, g = image(2000, 1500, spec, 163), image(300, 200, other, 164)
+    u, v = torch.empty_like(f), torch.empty_like(g)
+    lib.rl_test_persist_ctas(7)  # 768 CTAs for the 32 x 24 tiles
+    lib.rl_test_persist_wait_ns(1)
+    try:
+        with rl.Batch(2) as b:
+            t1 = b.submit(spec, f, u, 40, 2000, 1500)
+            t2 = b.submit(other, g, v, 10, 300, 200)
+            with pytest.raises(rl.RLError) as e:
+                b.wait(t1)
+            assert e.value.status == rl.RL_ERR_TIMEOUT
+            assert "gave up" in e.value.message
+            b.wait(t2)
+            torch.cuda.synchronize()
+            assert torch.equal(v, alone(other, g, 10))
+            lib.rl_test_persist_wait_ns(0)
+            t3 = b.submit(spec, f, u, 20, 2000, 1500)
+            b.wait(t3)
+            assert b.query(t3)
+    finally:
+        lib.rl_test_persist_wait_ns(0)
+        lib.rl_test_persist_ctas(0)
+    torch.cuda.synchronize()
+    assert torch.equal(u, alone(spec, f, 20))
