@@ -47,7 +47,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_plain_2048.json")
 
 def source_sha() -> str:
     """Hash of every CUDA source and the ABI header: a DRAM-traffic capture
-    counts for this build only if it was taken on the same sources."""
+    counts only for the library built from the sources it was taken on."""
     h = hashlib.sha256()
     files = sorted(glob.glob(os.path.join(ROOT, "paper_1304_7211_gb300", "csrc", "*")))
     for path in files + [os.path.join(ROOT, "include", "rl.h")]:
@@ -77,7 +77,7 @@ def ingest_ncu(csv_path: str, out_path: str, workload: str, command: str) -> dic
     """Per-kernel launches, DRAM bytes and device time per launch from an ncu
     CSV (``--csv --page raw``: one row per launch, a row of units under the
     header) of gpu__time_duration.sum and dram__bytes_{read,write}.sum,
-    tagged with the source hash of this build."""
+    tagged with the hash of the current sources."""
     import csv
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
              "nsecond": 1e-9, "ns": 1e-9, "usecond": 1e-6, "us": 1e-6, "msecond": 1e-3, "ms": 1e-3,
@@ -111,7 +111,7 @@ def ingest_ncu(csv_path: str, out_path: str, workload: str, command: str) -> dic
 
 
 def measured_traffic():
-    """The DRAM-traffic capture of this build (profiles/), or None when the
+    """The DRAM-traffic capture of the current sources (profiles/), or None when the
     sources changed since it was taken."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
@@ -641,7 +641,7 @@ def main():
     ap.add_argument("--no-config1", action="store_true", help="skip the 256^2 sub-measurement")
     ap.add_argument("--ingest-ncu", nargs=2, metavar=("CSV", "COMMAND"), default=None,
                     help="write profiles/traffic_plain_2048.json from an ncu CSV (launch list with "
-                         "dram__bytes_{read,write}.sum) of COMMAND, tagged with this build's source hash")
+                         "dram__bytes_{read,write}.sum) of COMMAND, tagged with the current sources' hash")
     args = ap.parse_args()
     if args.ingest_ncu:
         out = ingest_ncu(args.ingest_ncu[0], TRAFFIC_FILE, WORKLOAD, args.ingest_ncu[1])
@@ -767,7 +767,7 @@ def main():
     roof = dict(rooflines[dom])
     roof["per_solve"] = rooflines
     roof["traffic_capture"] = (os.path.relpath(TRAFFIC_FILE, ROOT) if cap is not None else
-                               "none for this build's sources (profiles/ capture predates a kernel change)")
+                               "none for the current sources (profiles/ capture predates a kernel change)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
