@@ -283,6 +283,75 @@ def thinning(threshold: float, relative: bool = True, reset_period: int = 10,
     return t
 
 
+STORAGE_DTYPE = {"f32": "float32", "bf16": "bfloat16", "f16": "float16"}
+
+
+def _image_view(x, name: str) -> tuple:
+    """(H, W, row pitch in elements, element stride along x, dtype name,
+    CUDA device index or None) of a 2-D torch tensor or numpy array.  The
+    stride of a dimension of extent 1 is never used, so a single row reads
+    as pitch W and a single column as element stride 1."""
+    if hasattr(x, "data_ptr") and hasattr(x, "stride") and callable(x.stride):  # torch tensor
+        if x.dim() != 2:
+            raise ValueError(f"{name} must be a 2-D image, got {x.dim()} dimensions")
+        dev = x.device.index if x.is_cuda else None
+        H, W, pitch, sx, dt = x.shape[0], x.shape[1], x.stride(0), x.stride(1), str(x.dtype)
+        dt = dt.replace("torch.", "")
+    elif hasattr(x, "ctypes") and hasattr(x, "strides"):  # numpy array
+        if x.ndim != 2:
+            raise ValueError(f"{name} must be a 2-D image, got {x.ndim} dimensions")
+        es = x.itemsize
+        if x.strides[0] % es or x.strides[1] % es:
+            raise ValueError(f"{name}: strides must be whole elements")
+        H, W, pitch, sx, dt, dev = x.shape[0], x.shape[1], x.strides[0] // es, x.strides[1] // es, \
+            str(x.dtype), None
+    else:
+        raise TypeError(f"{name} must be a torch tensor or a numpy array, got {type(x)}")
+    if W == 1:
+        sx = 1
+    if H == 1 and sx == 1:
+        pitch = W
+    return H, W, pitch, sx, dt, dev
+
+
+def check_images(storage: str, f, u0=None, out=None, device: int | None = None) -> tuple:
+    """Check that f, u0 and out describe one image layout the C call can take
+    with a single (W, H, pitch): 2-D, pixels contiguous along x, the storage
+    element type of the context, one row pitch >= W for all three, and CUDA
+    tensors on the context's device.  Returns (W, H, pitch).  A mismatch
+    would make the library read or write past a buffer, so it raises here."""
+    if not isinstance(storage, str):
+        storage = {v: k for k, v in STORAGE.items()}[storage]
+    want = STORAGE_DTYPE[storage]
+    H, W, pitch, sx, dt, dev = _image_view(f, "f")
+    if H < 1 or W < 1:
+        raise ValueError(f"f is empty ({H}x{W})")
+    if sx != 1 or pitch < W:
+        raise ValueError("f: pixels along a row must be contiguous and rows must not overlap "
+                         f"(strides {pitch}, {sx})")
+    for name, x, d in (("f", f, dev), ("u0", u0, None), ("out", out, None)):
+        if x is None:
+            continue
+        if x is not f:
+            h, w, p, s, dt, d = _image_view(x, name)
+            if (h, w) != (H, W) or s != 1 or p != pitch:
+                raise ValueError(f"{name} must be a {H}x{W} image with contiguous rows of pitch {pitch} "
+                                 f"(the layout of f); got {h}x{w}, strides ({p}, {s})")
+        if dt != want:
+            raise TypeError(f"{name} has element type {dt}; this context stores {want}")
+        if d is not None and device is not None and d != device:
+            raise ValueError(f"{name} is on cuda:{d}; this context runs on cuda:{device}")
+    return W, H, pitch
+
+
+def _empty_like_layout(f, H: int, W: int, pitch: int):
+    """An uninitialised image with the dtype, device and row pitch of f."""
+    if hasattr(f, "new_empty_strided"):
+        return f.new_empty_strided((H, W), (pitch, 1))
+    import numpy as np
+    return np.empty((H, pitch), dtype=f.dtype)[:, :W]
+
+
 class Deconvolver:
     """Owns one context and one PSF; runs RL on torch tensors or numpy arrays.
 
@@ -332,20 +401,10 @@ class Deconvolver:
 
     def run(self, f, iterations: int, u0=None, out=None, thin: rl_thinning | None = None,
             stats: bool = False):
-        H, W = f.shape[-2], f.shape[-1]
+        W, H, pitch = check_images(self.storage, f, u0, out, self.device)
         self._last_hw = (H, W)
-        if hasattr(f, "stride") and callable(f.stride):
-            pitch = f.stride(-2)
-        else:
-            if not f.flags["C_CONTIGUOUS"]:
-                raise ValueError("numpy inputs must be C-contiguous")
-            pitch = W
         if out is None:
-            if hasattr(f, "new_empty"):
-                out = f.new_empty(f.shape)
-            else:
-                import numpy as np
-                out = np.empty_like(f)
+            out = _empty_like_layout(f, H, W, pitch)
         st = rl_iterate(self.ctx, f, u0, out, W, H, pitch, iterations, thin, stats)
         return (out, st) if stats else out
 

@@ -201,3 +201,68 @@ def test_fifo_baseline_is_a_single_server_queue():
     assert rep.mean_ms == pytest.approx(lat.mean())
     assert rep.px_it == 3 * 100 * 5
     assert rep.mpx_it_per_s == pytest.approx(1500 / 4.0 / 1e6)
+
+
+# ---- Deconvolver.run: one image layout for f, u0 and out -------------------
+
+def test_image_layout_checks():
+    """Deconvolver.run hands f, u0 and out to the C call with a single
+    (W, H, pitch); layouts that call could not describe are refused before
+    it (they would make the library read or write past a buffer)."""
+    import torch
+    from paper_1304_7211_gb300 import rl
+    f = torch.rand(33, 50)
+    assert rl.check_images("f32", f) == (50, 33, 50)
+    assert rl.check_images(rl.RL_STORAGE_F32, f) == (50, 33, 50)
+    # a padded view: the pitch is its row stride, and a new output gets the same
+    wide = torch.rand(33, 87)
+    view = wide[:, :50]
+    assert rl.check_images("f32", view, u0=torch.rand(33, 87)[:, :50]) == (50, 33, 87)
+    out = rl._empty_like_layout(view, 33, 50, 87)
+    assert out.shape == (33, 50) and out.stride() == (87, 1) and out.dtype == torch.float32
+    assert rl.check_images("f32", view, out=out) == (50, 33, 87)
+    with pytest.raises(ValueError):  # a packed output for a padded input
+        rl.check_images("f32", view, out=torch.empty(33, 50))
+    # numpy, contiguous and padded
+    a = np.zeros((20, 30), np.float32)
+    assert rl.check_images("f32", a) == (30, 20, 30)
+    b = np.zeros((20, 64), np.float32)[:, :30]
+    assert rl.check_images("f32", b) == (30, 20, 64)
+    nb = rl._empty_like_layout(b, 20, 30, 64)
+    assert nb.shape == (20, 30) and nb.strides == (256, 4)
+    # element type must be the context's storage
+    with pytest.raises(TypeError):
+        rl.check_images("f32", f.to(torch.bfloat16))
+    with pytest.raises(TypeError):
+        rl.check_images("bf16", f)
+    assert rl.check_images("bf16", f.to(torch.bfloat16)) == (50, 33, 50)
+    with pytest.raises(TypeError):
+        rl.check_images("f32", a.astype(np.float64))
+    with pytest.raises(TypeError):
+        rl.check_images("f32", f, u0=f.double())
+    # shape, strides, dimensions
+    with pytest.raises(ValueError):
+        rl.check_images("f32", f.t())                   # columns contiguous
+    with pytest.raises(ValueError):
+        rl.check_images("f32", torch.rand(1, 50).expand(33, 50))  # rows overlap
+    with pytest.raises(ValueError):
+        rl.check_images("f32", torch.rand(2, 33, 50))
+    with pytest.raises(ValueError):
+        rl.check_images("f32", f, u0=torch.rand(33, 49))
+    with pytest.raises(ValueError):
+        rl.check_images("f32", torch.rand(0, 5))
+    with pytest.raises(TypeError):
+        rl.check_images("f32", [[1.0]])
+
+
+def test_image_layout_single_rows_and_columns():
+    """Strides of extent-1 dimensions carry no layout: a single row taken out
+    of a transposed column, or a single column of a wide image, is accepted
+    with the pitch that describes it."""
+    import torch
+    from paper_1304_7211_gb300 import rl
+    row = torch.rand(40, 1).t()                 # shape (1, 40), strides (1, 1)
+    assert rl.check_images("f32", row) == (40, 1, 40)
+    col = torch.rand(30, 9)[:, 4:5]             # shape (30, 1), strides (9, 1)
+    assert rl.check_images("f32", col) == (1, 30, 9)
+    assert rl.check_images("f32", np.zeros((30, 9), np.float32)[:, 4:5]) == (1, 30, 9)
