@@ -173,6 +173,7 @@ def rl_create(device: int = 0, stream=None, storage="f32", boundary="mirror", pa
     h = ctypes.c_void_p()
     rc = load().rl_create(ctypes.byref(cfg), ctypes.byref(h))
     _check(rc, None)
+    _CTX_ESIZE[h.value] = ESIZE.get(cfg.storage)
     return h
 
 
@@ -203,6 +204,43 @@ def rl_set_psf(ctx, spec_or_desc) -> None:
     del keep
 
 
+ESIZE = {RL_STORAGE_F32: 4, RL_STORAGE_BF16: 2, RL_STORAGE_F16: 2}
+_CTX_ESIZE = {}  # context handle -> bytes per stored image element
+
+
+def _ctx_esize(ctx):
+    return _CTX_ESIZE.get(getattr(ctx, "value", ctx))
+
+
+def _bytes_from(x) -> int | None:
+    """Bytes from the first element of a torch tensor or numpy array to the
+    end of the memory it lies in, or None when that is not known."""
+    if hasattr(x, "untyped_storage"):
+        return x.untyped_storage().nbytes() - x.storage_offset() * x.element_size()
+    if hasattr(x, "ctypes") and hasattr(x, "nbytes"):
+        root = x
+        while getattr(root, "base", None) is not None and hasattr(root.base, "ctypes"):
+            root = root.base
+        if root.base is not None:
+            return None
+        return root.ctypes.data + root.nbytes - x.ctypes.data
+    return None
+
+
+def _check_span(name: str, x, W: int, H: int, pitch: int, esize: int | None) -> None:
+    """Refuse an image buffer (torch tensor or numpy array) that ends before
+    the last pixel a C call with (W, H, pitch) would touch: (H - 1) pitch + W
+    elements of the context's storage type.  Raw addresses are the caller's
+    responsibility; sizes the library rejects itself are left to it."""
+    if x is None or isinstance(x, int) or esize is None or W < 1 or H < 1 or pitch < W:
+        return
+    have = _bytes_from(x)
+    need = ((H - 1) * pitch + W) * esize
+    if have is not None and have < need:
+        raise ValueError(f"{name} holds {have} bytes from its start; W={W}, H={H}, pitch={pitch} "
+                         f"need {need}")
+
+
 def _addr(x) -> int | None:
     if x is None:
         return None
@@ -219,6 +257,9 @@ def rl_iterate(ctx, f, u0, u_out, W: int, H: int, pitch: int, iterations: int,
                thinning: rl_thinning | None = None, stats: bool = False):
     """Run RL iterations; returns an ``rl_stats`` when ``stats`` is true."""
     st = rl_stats() if stats else None
+    es = _ctx_esize(ctx)
+    for name, x in (("f", f), ("u0", u0), ("u_out", u_out)):
+        _check_span(name, x, W, H, pitch, es)
     rc = load().rl_iterate(ctx, _addr(f), _addr(u0), _addr(u_out), W, H, pitch, iterations,
                            ctypes.byref(thinning) if thinning is not None else None,
                            ctypes.byref(st) if st is not None else None)
@@ -231,7 +272,10 @@ def rl_iterate_tiles(ctx, jobs) -> None:
     ``(f, u0, u_out, W, H, pitch, iterations)`` on the device, all under the
     context's PSF (disc or box kernel)."""
     arr = (rl_job * max(len(jobs), 1))()
+    es = _ctx_esize(ctx)
     for i, (f, u0, u_out, W, H, pitch, iterations) in enumerate(jobs):
+        for name, x in (("f", f), ("u0", u0), ("u_out", u_out)):
+            _check_span(f"job {i}: {name}", x, W, H, pitch, es)
         arr[i] = rl_job(_addr(f), _addr(u0), _addr(u_out), None, None, W, H, pitch, iterations,
                         rl_psf_desc(), None)
     rc = load().rl_iterate_tiles(ctx, arr, len(jobs))
@@ -270,6 +314,7 @@ def rl_motion_x_noalloc(f, u0, u_out, W: int, H: int, pitch: int, length: int,
 
 def rl_destroy(ctx) -> None:
     if ctx:
+        _CTX_ESIZE.pop(getattr(ctx, "value", ctx), None)
         load().rl_destroy(ctx)
 
 
@@ -423,6 +468,7 @@ class Batch:
         if rc != RL_OK:
             raise RLError(rc, "rl_batch_create failed")
         self.h = h
+        self.esize = ESIZE.get(cfg.storage)
 
     def _check(self, rc):
         if rc != RL_OK:
@@ -430,6 +476,10 @@ class Batch:
 
     def submit(self, spec, f, u_out, iterations: int, W: int, H: int, pitch: int | None = None,
                u0=None, f_host=None, u_host=None, thin: rl_thinning | None = None) -> int:
+        for name, x in (("f", f), ("u0", u0), ("u_out", u_out)):
+            _check_span(name, x, W, H, pitch or W, self.esize)
+        for name, x in (("f_host", f_host), ("u_host", u_host)):  # packed rows
+            _check_span(name, x, W, H, W, self.esize)
         d, keep = psf_desc(spec)
         job = rl_job(_addr(f), _addr(u0), _addr(u_out), _addr(f_host), _addr(u_host), W, H,
                      pitch or W, iterations, d,

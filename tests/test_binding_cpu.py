@@ -266,3 +266,33 @@ def test_image_layout_single_rows_and_columns():
     col = torch.rand(30, 9)[:, 4:5]             # shape (30, 1), strides (9, 1)
     assert rl.check_images("f32", col) == (1, 30, 9)
     assert rl.check_images("f32", np.zeros((30, 9), np.float32)[:, 4:5]) == (1, 30, 9)
+
+
+def test_buffer_span_checks():
+    """The low-level calls take (W, H, pitch) from the caller; a tensor or
+    array that ends before the last pixel those describe is refused before
+    the C call (it would read or write past the buffer)."""
+    import torch
+    from paper_1304_7211_gb300 import rl
+    f = torch.zeros(10, 16)
+    rl._check_span("f", f, 16, 10, 16, 4)                 # exactly the buffer
+    rl._check_span("f", f, 12, 10, 16, 4)                 # a pitched sub-image
+    rl._check_span("f", f.to(torch.bfloat16), 16, 10, 16, 2)
+    with pytest.raises(ValueError):
+        rl._check_span("f", f, 16, 11, 16, 4)             # one row too many
+    with pytest.raises(ValueError):
+        rl._check_span("f", f, 16, 10, 17, 4)             # pitch past the rows
+    with pytest.raises(ValueError):                       # bf16 buffer, f32 context
+        rl._check_span("f", f.to(torch.bfloat16), 16, 10, 16, 4)
+    with pytest.raises(ValueError):                       # a view starting inside the buffer
+        rl._check_span("f", f[1:], 16, 10, 16, 4)
+    rl._check_span("f", f[1:], 16, 9, 16, 4)
+    a = np.zeros((10, 16), np.float32)
+    rl._check_span("a", a, 16, 10, 16, 4)
+    rl._check_span("a", a[2:, 3:], 13, 8, 16, 4)          # ends exactly at the last element
+    with pytest.raises(ValueError):
+        rl._check_span("a", a[2:, 3:], 14, 8, 16, 4)
+    # left to the library: raw addresses, unknown storage, sizes it rejects
+    rl._check_span("p", 12345, 16, 10, 16, 4)
+    rl._check_span("f", f, 16, 11, 16, None)
+    rl._check_span("f", f, 16, 10, 8, 4)
