@@ -493,28 +493,23 @@ def serve_run(local, n=400, rates=(100.0, 200.0), slots=16):
             "rates": rows}
 
 
-def thinned_run(local, size=4096, iters=300, oracle_size=384):
+def thinned_run(local, size=4096, iters=300, oracle_size=384, pending=None):
     """Thinned workload: disc radius 12, Poisson noise at peak 500, 300
     iterations, relative thresholds {1e-3, 1e-4, 1e-5} with the mask
     recomputed every 10 iterations, FP32 and BF16 storage.  Reports time,
-    active pixel-iterations, PSNR against the latent image, and the error
-    against the FP64 oracle on a smaller image of the same generator."""
+    active pixel-iterations and PSNR against the latent image; each variant
+    also runs on a smaller image of the same generator, whose error against
+    the FP64 oracle the CPU-baseline leg fills in (``pending``)."""
     import numpy as np
     import torch
-    import oracle
     from paper_1304_7211_gb300 import rl, synth
     c = synth.config3(size)
     rows = []
     variants = [(None, "f32"), (None, "bf16")] + [(t, sto) for t in (1e-3, 1e-4, 1e-5)
                                                    for sto in ("f32", "bf16")]
     small = synth.config3(oracle_size)
-    t0 = time.perf_counter()
-    refs = {}
-    for tau in (None, 1e-3, 1e-4, 1e-5):
-        fsm = small.f.astype(np.float32).astype(np.float64)
-        refs[tau] = oracle.rl(fsm, oracle.psf_disc(12), iters, threshold=tau,
-                              update_period=10).u
-    oracle_s = time.perf_counter() - t0
+    outputs = []
+    key = f"rel_linf_vs_oracle_{oracle_size}"
     for tau, sto in variants:
         dt = {"f32": torch.float32, "bf16": torch.bfloat16}[sto]
         f = torch.from_numpy(c.f.astype(np.float32)).to(dt).cuda(local)
@@ -523,17 +518,24 @@ def thinned_run(local, size=4096, iters=300, oracle_size=384):
         with rl.Deconvolver(c.spec, device=local, storage=sto) as d:
             rl.rl_iterate(d.ctx, f, None, u, size, size, size, 20, th)  # warm-up
             st = rl.rl_iterate(d.ctx, f, None, u, size, size, size, iters, th, stats=True)
-            psnr = oracle.psnr_db(u.float().cpu().numpy(), c.g)
+            psnr = psnr_db(u.float().cpu().numpy(), c.g)
             fs = torch.from_numpy(small.f.astype(np.float32)).to(dt).cuda(local)
             us = torch.empty_like(fs)
             rl.rl_iterate(d.ctx, fs, None, us, oracle_size, oracle_size, oracle_size, iters, th)
-            err = oracle.rel_linf(us.float().cpu().numpy(), refs[tau])
-        rows.append({"tau": tau, "storage": sto, "ms": st.device_ms,
-                     "mpx_it_per_s": size * size * iters / st.device_ms / 1e3,
-                     "active_pct": 100.0 * st.active_pixel_iterations / st.pixel_iterations,
-                     "psnr_vs_latent_db": psnr, f"rel_linf_vs_oracle_{oracle_size}": err})
-    return {"workload": f"{size}^2 disc r12 Poisson peak 500, {iters} it, mask every 10 it",
-            "oracle_cpu_s": oracle_s, "rows": rows}
+            u_small = us.float().cpu().numpy()
+        row = {"tau": tau, "storage": sto, "ms": st.device_ms,
+               "mpx_it_per_s": size * size * iters / st.device_ms / 1e3,
+               "active_pct": 100.0 * st.active_pixel_iterations / st.pixel_iterations,
+               "psnr_vs_latent_db": psnr, key: None}
+        rows.append(row)
+        outputs.append((row, tau, u_small))
+    out = {"workload": f"{size}^2 disc r12 Poisson peak 500, {iters} it, mask every 10 it",
+           "oracle_cpu_s": None, "rows": rows}
+    if pending is not None:
+        # the oracle runs on the input as the GPU saw it (FP32-rounded f)
+        pending.append({"kind": "thinned", "f": small.f.astype(np.float32).astype(np.float64),
+                        "iters": iters, "outputs": outputs, "key": key, "report": out})
+    return out
 
 
 def solve_roofline(spec, ms_solve, launches, pk, pk_kind, sms, cap) -> dict:
@@ -583,12 +585,12 @@ def solve_roofline(spec, ms_solve, launches, pk, pk_kind, sms, cap) -> dict:
             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"}
 
 
-def config1_run(local) -> dict:
+def config1_run(local, pending=None) -> dict:
     """The 256^2 workload: motion-x 15, Gaussian noise sigma 2, 50 iterations,
-    FP32; rate and the error against the FP64 oracle on the same input."""
+    FP32; its rate, and its output for the CPU-baseline leg to compare with
+    the FP64 oracle on the same input (``pending``)."""
     import numpy as np
     import torch
-    import oracle
     from paper_1304_7211_gb300 import rl, synth
     c = synth.config1()
     f32 = c.f.astype(np.float32)
@@ -599,14 +601,53 @@ def config1_run(local) -> dict:
         rl.rl_iterate(d.ctx, f, None, u, W, H, W, c.iterations)
         ms = sorted(rl.rl_iterate(d.ctx, f, None, u, W, H, W, c.iterations, stats=True).device_ms
                     for _ in range(7))
-    t = c.spec.dense()
-    ref = oracle.rl(f32.astype(np.float64), oracle.psf_dense(t, t.shape[1] // 2, t.shape[0] // 2),
-                    c.iterations).u
     med = ms[len(ms) // 2]
-    return {"workload": f"{W}x{H} fp32, motion-x 15, Gaussian noise sigma 2, {c.iterations} it",
-            "value": W * H * c.iterations / med / 1e3, "unit": UNIT, "ms_per_solve": med,
-            "rel_linf_vs_oracle": oracle.rel_linf(u.cpu().numpy(), ref),
-            "timing": "CUDA events around rl_iterate (stats), median of 7; latency-bound at this size"}
+    out = {"workload": f"{W}x{H} fp32, motion-x 15, Gaussian noise sigma 2, {c.iterations} it",
+           "value": W * H * c.iterations / med / 1e3, "unit": UNIT, "ms_per_solve": med,
+           "rel_linf_vs_oracle": None,
+           "timing": "CUDA events around rl_iterate (stats), median of 7; latency-bound at this size"}
+    if pending is not None:
+        pending.append({"kind": "config1", "f": f32.astype(np.float64), "taps": c.spec.dense(),
+                        "iters": c.iterations, "u": u.cpu().numpy(), "report": out})
+    return out
+
+
+def rel_linf(a, b) -> float:
+    """Relative L-infinity difference max|a - b| / max|b| (FP64)."""
+    import numpy as np
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def psnr_db(u, g) -> float:
+    """PSNR of u against the latent image g, peak = max(g)."""
+    import numpy as np
+    u, g = np.asarray(u, np.float64), np.asarray(g, np.float64)
+    mse = float(np.mean((u - g) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(float(g.max()) ** 2 / mse)
+
+
+def oracle_checks(pending) -> float:
+    """The CPU-baseline leg's comparisons: the FP64 oracle run on the inputs
+    of the GPU sub-measurements (``pending``), its relative L-inf difference
+    written into their reports.  Returns the oracle's seconds."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for p in pending:
+        if p["kind"] == "config1":
+            t = p["taps"]
+            ref = oracle.rl(p["f"], oracle.psf_dense(t, t.shape[1] // 2, t.shape[0] // 2), p["iters"]).u
+            p["report"]["rel_linf_vs_oracle"] = rel_linf(p["u"], ref)
+        elif p["kind"] == "thinned":
+            refs = {}
+            for row, tau, u in p["outputs"]:
+                if tau not in refs:
+                    refs[tau] = oracle.rl(p["f"], oracle.psf_disc(12), p["iters"], threshold=tau,
+                                          update_period=10).u
+                row[p["key"]] = rel_linf(u, refs[tau])
+            p["report"]["oracle_cpu_s"] = time.perf_counter() - t0
+    return time.perf_counter() - t0
 
 
 def main():
@@ -657,8 +698,13 @@ def main():
         torch.cuda.set_device(local)
         from paper_1304_7211_gb300 import _build
         _build.build()
-        out = (thinned_run(local) if args.workload == "thinned"
-               else serve_run(local, n=2000, rates=(20.0, 50.0, 100.0, 200.0)))
+        if args.workload == "thinned":
+            pending = []
+            out = thinned_run(local, pending=pending)
+            if not args.no_cpu_baseline:
+                oracle_checks(pending)  # the CPU-baseline leg of this mode
+        else:
+            out = serve_run(local, n=2000, rates=(20.0, 50.0, 100.0, 200.0))
         print(json.dumps(out), flush=True)
         return 0
 
@@ -780,8 +826,9 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "clocks": clk}
     progress("main step, e2e and rooflines")
+    pending = []  # GPU outputs the CPU-baseline leg compares with the oracle
     if not args.no_config1:
-        line["config1"] = config1_run(local)
+        line["config1"] = config1_run(local, pending)
         progress("config1")
     if not args.no_batch:
         line["batch"] = batch_run(local)
@@ -791,13 +838,15 @@ def main():
         line["batch_tiles"] = tiles_run(local)
         progress("batch tiles")
     if not args.no_config3 and ws == 1:
-        line["config3"] = thinned_run(local)
+        line["config3"] = thinned_run(local, pending=pending)
         progress("config3")
     if not args.no_serve:
         line["serve"] = serve_run(local, n=args.serve_requests)
         progress("serve")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(inputs)
+        if pending:
+            line["cpu_baseline"]["oracle_checks_s"] = oracle_checks(pending)
         progress("cpu baseline")
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -296,3 +296,40 @@ def test_buffer_span_checks():
     rl._check_span("p", 12345, 16, 10, 16, 4)
     rl._check_span("f", f, 16, 11, 16, None)
     rl._check_span("f", f, 16, 10, 8, 4)
+
+
+def test_bench_oracle_checks_fill_the_sub_line_reports():
+    """The oracle comparisons of the bench's 256^2 and thinned sub-lines run
+    in its CPU-baseline leg: the pending GPU outputs get their relative L-inf
+    difference from the oracle written into the reports they came from."""
+    import bench
+    import oracle
+    rng = np.random.default_rng(5)
+    f = rng.uniform(10, 200, size=(30, 34))
+    taps = np.ones((1, 5)) / 5
+    psf = oracle.psf_dense(taps, 2, 0)
+    u = oracle.rl(f, psf, 4).u
+    rep1 = {"rel_linf_vs_oracle": None}
+    pend = [{"kind": "config1", "f": f, "taps": taps, "iters": 4, "u": u * (1 + 1e-3), "report": rep1}]
+    g = rng.uniform(10, 200, size=(28, 27))
+    rows = [{"k": None}, {"k": None}, {"k": None}]
+    plain = oracle.rl(g, oracle.psf_disc(12), 3).u
+    thin = oracle.rl(g, oracle.psf_disc(12), 3, threshold=1e-3, update_period=10).u
+    rep3 = {"oracle_cpu_s": None, "rows": rows}
+    pend.append({"kind": "thinned", "f": g, "iters": 3, "key": "k", "report": rep3,
+                 "outputs": [(rows[0], None, plain), (rows[1], 1e-3, thin), (rows[2], None, plain + 1.0)]})
+    secs = bench.oracle_checks(pend)
+    assert secs >= 0 and rep3["oracle_cpu_s"] is not None
+    assert rep1["rel_linf_vs_oracle"] == pytest.approx(1e-3 * np.max(np.abs(u)) / np.max(np.abs(u)), rel=1e-6)
+    assert rows[0]["k"] == 0.0 and rows[1]["k"] == 0.0
+    assert rows[2]["k"] == pytest.approx(1.0 / np.max(np.abs(plain)))
+
+
+def test_bench_metrics_match_the_oracle_definitions():
+    import bench
+    import oracle
+    rng = np.random.default_rng(6)
+    a, b = rng.normal(size=(9, 11)), rng.normal(size=(9, 11)) + 3
+    assert bench.rel_linf(a, b) == pytest.approx(oracle.rel_linf(a, b), rel=1e-12)
+    assert bench.psnr_db(a, b) == pytest.approx(oracle.psnr_db(a, b), rel=1e-12)
+    assert bench.psnr_db(b, b) == float("inf")
