@@ -351,6 +351,31 @@ def test_poisson_likelihood_catches_an_inverted_ratio():
     assert loglik(wrong_step(f)) < loglik(f)
 
 
+def test_scaling_the_data_scales_the_iterates():
+    """Eq. 3 is homogeneous of degree one in (f, u0): scaling f by 4 (exact
+    in binary floating point) scales every iterate by 4 bit for bit.  The
+    relative rule of Eq. 4-5 (|c - 1|) is scale-free, so the same masks
+    result; the absolute rule (|u' - u|) needs the threshold scaled too, and
+    with the threshold left alone it decides differently.  A rule that mixed
+    the two changes, or a constant added anywhere in the arithmetic, fails."""
+    rng = np.random.default_rng(21)
+    psf = oracle.psf_disc(2)
+    g = rng.uniform(10, 250, size=(16, 15))
+    f = rng.poisson(oracle.conv(g, psf, "mirror")).astype(np.float64) + 1.0
+    K = 13
+    np.testing.assert_array_equal(oracle.rl(4 * f, psf, K).u, 4 * oracle.rl(f, psf, K).u)
+    a = oracle.rl(f, psf, K, threshold=2e-3, relative=True)
+    b = oracle.rl(4 * f, psf, K, threshold=2e-3, relative=True)
+    np.testing.assert_array_equal(b.u, 4 * a.u)
+    assert a.active_pixel_iterations == b.active_pixel_iterations
+    a = oracle.rl(f, psf, K, threshold=0.05, relative=False)
+    b = oracle.rl(4 * f, psf, K, threshold=0.2, relative=False)
+    np.testing.assert_array_equal(b.u, 4 * a.u)
+    assert a.active_pixel_iterations == b.active_pixel_iterations
+    c = oracle.rl(4 * f, psf, K, threshold=0.05, relative=False)
+    assert c.active_pixel_iterations > a.active_pixel_iterations  # same threshold, larger changes
+
+
 def test_zero_ratio_where_reblur_vanishes():
     # f = 0 on a block wider than the PSF: v = 0 there after one step,
     # q must be 0 (not NaN) and u stays finite.
