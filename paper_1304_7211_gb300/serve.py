@@ -116,8 +116,8 @@ class Server:
                     break
                 H, W = r.f.shape
                 on_dev = hasattr(r.f, "is_cuda") and r.f.is_cuda
-                if on_dev:
-                    f_dev, f_host = r.f, None
+                if on_dev:  # in the server's storage type (a converted copy if it differs)
+                    f_dev, f_host = (r.f if r.f.dtype == self.dtype else r.f.to(self.dtype)), None
                 else:
                     f_dev = torch.empty((H, W), dtype=self.dtype, device=dev)
                     f_host = torch.from_numpy(np.ascontiguousarray(r.f)).to(self.dtype).pin_memory()
