@@ -173,7 +173,8 @@ def service_times(requests: list[Request], device: int = 0, storage: str = "f32"
         t0 = time.perf_counter()
         with rl.Deconvolver(r.spec, device=device, storage=storage, boundary=boundary) as d:
             on_dev = hasattr(r.f, "is_cuda") and r.f.is_cuda
-            f = r.f if on_dev else torch.from_numpy(np.ascontiguousarray(r.f)).to(dtype).cuda(device)
+            f = (r.f.to(dtype) if on_dev else
+                 torch.from_numpy(np.ascontiguousarray(r.f)).to(dtype).cuda(device))
             th = rl.thinning(*r.thin) if r.thin else None
             u = d.run(f, r.iterations, thin=th)
             r.result = u.float().cpu().numpy()
