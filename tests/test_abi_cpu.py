@@ -72,3 +72,63 @@ def test_create_fails_loudly_without_gpu(lib):
     with pytest.raises(rl.RLError) as ei:
         rl.rl_create(0)
     assert ei.value.status in (rl.RL_ERR_CUDA, rl.RL_ERR_INVALID_ARG)
+
+
+def test_batch_calls_validate_without_gpu(lib):
+    """The batch calls check their arguments before any CUDA call: NULL
+    handles and slot counts out of range come back as statuses."""
+    import ctypes
+    from paper_1304_7211_gb300 import rl
+    h = ctypes.c_void_p()
+    cfg = rl.rl_config(0, None, 0, 0, 0, 0)
+    assert lib.rl_batch_create(ctypes.byref(cfg), 0, ctypes.byref(h)) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_create(ctypes.byref(cfg), 257, ctypes.byref(h)) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_create(ctypes.byref(cfg), 1, None) == rl.RL_ERR_INVALID_ARG
+    t, done, running = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+    assert lib.rl_batch_submit(None, None, ctypes.byref(t)) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_query(None, 1, ctypes.byref(done)) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_wait(None, 1) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_sync(None) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_cancel(None, 1, ctypes.byref(running)) == rl.RL_ERR_INVALID_ARG
+    assert lib.rl_batch_destroy(None) == rl.RL_OK
+    assert lib.rl_batch_last_error(None) == b""
+    assert lib.rl_get_mask(None, None, 0) == rl.RL_ERR_INVALID_ARG
+
+
+def test_batch_create_fails_loudly_without_gpu(lib):
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1304_7211_gb300 import rl
+    h = ctypes.c_void_p()
+    cfg = rl.rl_config(0, None, 0, 0, 0, 0)
+    st = lib.rl_batch_create(ctypes.byref(cfg), 2, ctypes.byref(h))
+    assert st != rl.RL_OK and not h.value
+
+
+def test_noalloc_entry_point_checks_before_touching_the_gpu(lib):
+    """rl_motion_x_noalloc validates pointers, sizes and the fixed scratch
+    limit before any CUDA call (the pointer values here are never
+    dereferenced): each case returns RL_ERR_INVALID_ARG with a message."""
+    import ctypes
+    from paper_1304_7211_gb300 import rl
+    buf = ctypes.create_string_buffer(256)
+
+    def call(f, u0, out, W, H, pitch, length=9, boundary=rl.RL_BOUNDARY_MIRROR, its=3):
+        buf.value = b""
+        st = lib.rl_motion_x_noalloc(f, u0, out, W, H, pitch, length, boundary, its, None, buf, len(buf))
+        return st, buf.value.decode()
+
+    F, U0, OUT = 0x1000, 0x2000, 0x3000
+    st, msg = call(None, None, OUT, 64, 64, 64)
+    assert st == rl.RL_ERR_INVALID_ARG and "required" in msg
+    assert call(F, None, F, 64, 64, 64)[0] == rl.RL_ERR_INVALID_ARG      # u_out aliases f
+    assert call(F, OUT, OUT, 64, 64, 64)[0] == rl.RL_ERR_INVALID_ARG     # u_out aliases u0
+    assert call(F, None, OUT, 64, 64, 63)[0] == rl.RL_ERR_INVALID_ARG    # pitch < W
+    assert call(F, None, OUT, 64, 64, 64, boundary=7)[0] == rl.RL_ERR_INVALID_ARG
+    assert call(F, None, OUT, 64, 64, 64, its=-1)[0] == rl.RL_ERR_INVALID_ARG
+    assert call(F, None, OUT, 8, 64, 8, length=17)[0] == rl.RL_ERR_INVALID_ARG  # half length >= W
+    W, H = 4096, rl.RL_NOALLOC_MAX_PIXELS // 4096 + 1                   # one row past the limit
+    st, msg = call(F, None, OUT, W, H, W)
+    assert st == rl.RL_ERR_INVALID_ARG and str(rl.RL_NOALLOC_MAX_PIXELS) in msg
