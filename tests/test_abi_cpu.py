@@ -132,3 +132,15 @@ def test_noalloc_entry_point_checks_before_touching_the_gpu(lib):
     W, H = 4096, rl.RL_NOALLOC_MAX_PIXELS // 4096 + 1                   # one row past the limit
     st, msg = call(F, None, OUT, W, H, W)
     assert st == rl.RL_ERR_INVALID_ARG and str(rl.RL_NOALLOC_MAX_PIXELS) in msg
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the shared library missing, every call through the
+    binding raises instead of computing anything elsewhere."""
+    from paper_1304_7211_gb300 import rl, synth
+    monkeypatch.setattr(rl, "_lib", None)
+    monkeypatch.setattr(rl, "LIB_PATH", str(tmp_path / "librl_gb300.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        rl.load()
+    with pytest.raises(RuntimeError, match="missing"):
+        rl.Deconvolver(synth.disc(3))
