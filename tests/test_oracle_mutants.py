@@ -65,6 +65,18 @@ MUTANTS = {
     "disc_strict_inclusion": (
         "int in = dx * dx + dy * dy <= (long)r * r;",
         "int in = dx * dx + dy * dy < (long)r * r;"),
+    # with Q = P the mask rebuilt on every iteration instead of full ones only
+    "mask_update_every_iteration": (
+        "else if (full)\n                    M[p] = (uint8_t)(d >= tau);",
+        "else\n                    M[p] = (uint8_t)(use && d >= tau);"),
+    # dense taps left unnormalised
+    "taps_not_normalised": (
+        "for (int k = 0; k < n; ++k) h[k] /= s;",
+        "(void)s;"),
+    # motion anchor rounded the other way for even lengths
+    "motion_anchor_even": (
+        "*kw = length; *kh = 1; *ax = length / 2; *ay = 0;",
+        "*kw = length; *kh = 1; *ax = (length - 1) / 2; *ay = 0;"),
 }
 
 PLUGIN = """
